@@ -1,0 +1,172 @@
+/*
+ * slg.h -- s-line graphs of hypergraphs on one GB300 (sm_103a): C ABI.
+ *
+ * The operation (Section III, definition of L_s(H)): H = (V, E) has
+ * hyperedges e_0..e_{m-1}, each a set of vertices.  The weighted line graph
+ * joins e_i and e_j (i != j) with weight w_ij = |e_i ∩ e_j| when the two
+ * share a vertex; the s-line graph L_s(H) keeps the joins with w_ij >= s
+ * (s >= 1).  The same construction on the dual H* (vertices and hyperedges
+ * swapped, Section III) is selected with SLG_DUAL.
+ *
+ * Output format: the canonical edge list of L_s -- triples (i, j, w) with
+ * i < j, w = |e_i ∩ e_j| >= s, listed in ascending (i, j) order, as three
+ * int32 arrays (structure of arrays).  Ids are the caller's ids of the side
+ * that was computed (hyperedge ids of H, or vertex ids of H for SLG_DUAL).
+ * The result is unique and the library produces it bit for bit: every
+ * count is an exact integer.
+ *
+ * Input format (Section III, the incidence of H and its bipartite form):
+ * CSR (hyperedge -> vertices) and CSC (vertex -> hyperedges) of the same
+ * incidence, int32 offsets and ids, every row strictly ascending, nnz < 2^31.
+ *
+ * Memory: unless stated otherwise, array arguments are DEVICE pointers on
+ * the current CUDA device, owned by the caller, and are only read (inputs)
+ * or written (outputs) during the call.  The library allocates its own
+ * working memory from the device's stream-ordered pool and keeps a
+ * zero-initialised scratch area per device between calls.  Calls are
+ * enqueued on `stream` (a cudaStream_t; NULL = legacy default stream) and
+ * return after one device->host read of the pair count, so *n_pairs and the
+ * returned status are final on return; output arrays are complete once the
+ * stream reaches that point (they are, since the call synchronises on it).
+ *
+ * Errors: every entry point returns an slg_status.  The library never
+ * aborts the process and never traps the GPU: bad input detected on the
+ * device is reported through a status word that the host reads.
+ *
+ * Thread safety: calls on different streams may run concurrently from
+ * different host threads; the per-device scratch is guarded by a mutex.
+ */
+#ifndef SLG_H_
+#define SLG_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SLG_ABI_VERSION 1
+
+/* Incidence of H as CSR + CSC (Section III: the hyperedge/vertex incidence
+ * and its bipartite form).  All pointers are device pointers. */
+typedef struct slg_hypergraph {
+  int32_t n_edges;       /* m = |E|: rows of the CSR, >= 0 */
+  int32_t n_vertices;    /* n = |V|: rows of the CSC, >= 0 */
+  int64_t nnz;           /* number of incidences, 0 <= nnz < 2^31 */
+  const int32_t *e_off;  /* [m+1] CSR offsets, e_off[0] = 0, e_off[m] = nnz */
+  const int32_t *e_idx;  /* [nnz] vertex ids of each hyperedge, ascending */
+  const int32_t *v_off;  /* [n+1] CSC offsets, v_off[0] = 0, v_off[n] = nnz */
+  const int32_t *v_idx;  /* [nnz] hyperedge ids of each vertex, ascending */
+} slg_hypergraph;
+
+/* Status codes. */
+typedef enum slg_status {
+  SLG_OK = 0,
+  SLG_ERR_INVALID = 1,     /* bad argument or malformed incidence */
+  SLG_ERR_CAPACITY = 2,    /* output capacity < pair count; *n_pairs = count */
+  SLG_ERR_NOMEM = 3,       /* device allocation failed */
+  SLG_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+  SLG_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  SLG_ERR_UNSUPPORTED = 6  /* flag combination not provided */
+} slg_status;
+
+/* Flags (bitwise OR). */
+#define SLG_DUAL 0x1u        /* compute L_s(H*) instead of L_s(H) */
+#define SLG_UNWEIGHTED 0x2u  /* stop counting a pair once it reaches s
+                                (the short-circuit of Section IV-C); the
+                                pair set is unchanged, out_w is not written
+                                and may be NULL */
+/* Algorithm selector (mutually exclusive values in bits 8..11). */
+#define SLG_ALGO_MASK 0xF00u
+#define SLG_ALGO_BINNED 0x000u /* default: degree-binned wedge walk */
+#define SLG_ALGO_PLAIN 0x100u  /* plain per-hyperedge kernel: one warp per
+                                  hyperedge, global count array (the
+                                  paper's visited array), two passes */
+#define SLG_ALGO_SPGEMM 0x200u /* filtered SpGEMM: both triangles of B·Bᵀ,
+                                  no pruning, filter afterwards
+                                  (Section IV-D) */
+
+/*
+ * slg_count -- number of pairs of L_s (Section III) without writing them.
+ *   h        incidence of H (device arrays as described above)
+ *   s        overlap threshold, s >= 1 (s larger than every hyperedge gives 0)
+ *   flags    SLG_DUAL, SLG_UNWEIGHTED, one SLG_ALGO_* value
+ *   n_pairs  host pointer, receives |L_s|
+ *   stream   cudaStream_t to run on
+ * Returns SLG_OK, SLG_ERR_INVALID (s < 1, NULL pointers, negative sizes,
+ * nnz >= 2^31, offsets not monotone, ids out of range, rows not strictly
+ * ascending, CSR and CSC not the same incidence), SLG_ERR_NOMEM,
+ * SLG_ERR_CUDA.
+ */
+int slg_count(const slg_hypergraph *h, int32_t s, uint32_t flags,
+              int64_t *n_pairs, void *stream);
+
+/*
+ * slg_build -- the canonical edge list of L_s (Section III; Step 1 and
+ * Step 2 of Section IV: s-overlaps, then the edge list).
+ *   out_i, out_j, out_w  device int32 arrays of at least `capacity`
+ *                        elements; out_w may be NULL with SLG_UNWEIGHTED
+ *   capacity             elements available in each output array
+ *   n_pairs              host pointer, receives |L_s|
+ * When |L_s| > capacity the call returns SLG_ERR_CAPACITY with *n_pairs set
+ * to the required count and the outputs unspecified.  Other errors as for
+ * slg_count.
+ */
+int slg_build(const slg_hypergraph *h, int32_t s, uint32_t flags,
+              int32_t *out_i, int32_t *out_j, int32_t *out_w,
+              int64_t capacity, int64_t *n_pairs, void *stream);
+
+/*
+ * slg_build_rows -- rows [row_begin, row_end) of the canonical edge list
+ * (the pairs whose smaller id i lies in the range), for streaming an output
+ * that does not fit in memory at once.  Concatenating consecutive ranges
+ * gives slg_build's result.  0 <= row_begin <= row_end <= rows of the side.
+ */
+int slg_build_rows(const slg_hypergraph *h, int32_t s, uint32_t flags,
+                   int32_t row_begin, int32_t row_end, int32_t *out_i,
+                   int32_t *out_j, int32_t *out_w, int64_t capacity,
+                   int64_t *n_pairs, void *stream);
+
+/*
+ * slg_build_host -- slg_build with every array in HOST memory: the call
+ * copies the incidence to the device, builds L_s there and copies the
+ * triples back (end-to-end use from host data).  `h` holds host pointers.
+ * Pinned host memory makes the copies faster; pageable memory also works.
+ */
+int slg_build_host(const slg_hypergraph *h, int32_t s, uint32_t flags,
+                   int32_t *out_i, int32_t *out_j, int32_t *out_w,
+                   int64_t capacity, int64_t *n_pairs, void *stream);
+
+/*
+ * slg_wedges -- W_s, the number of upper-triangle wedges e -> v -> f
+ * (f > e, |e| >= s, |f| >= s) that the walk visits: the exact work of the
+ * s-overlap step after degree-based pruning (Section IV-C), equal to
+ * sum over vertices of C(d_s(v), 2).  Device computation; host result.
+ */
+int slg_wedges(const slg_hypergraph *h, int32_t s, uint32_t flags,
+               int64_t *wedges, void *stream);
+
+/* Statistics of the last call made by this host thread. */
+typedef struct slg_stats {
+  int64_t wedges;          /* W_s visited */
+  int64_t pairs;           /* |L_s| */
+  int64_t rows_active;     /* rows with size >= s */
+  int64_t rows_bin[4];     /* rows per bin: warp, cta-small, cta-large, giant */
+  int64_t wedges_bin[4];   /* wedges per bin */
+  int32_t kernel_launches; /* kernels launched by the call */
+  int32_t reserved;
+} slg_stats;
+
+int slg_last_stats(slg_stats *out);
+
+/* Human-readable text for a status code (static storage). */
+const char *slg_strerror(int status);
+
+/* SLG_ABI_VERSION of the loaded library. */
+int slg_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SLG_H_ */
