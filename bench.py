@@ -1,0 +1,421 @@
+#!/usr/bin/env python
+"""Benchmark of the s-line-graph build (the s-overlap hot path).
+
+One step builds the canonical edge list of L_s for s = 2 and s = 8 on the
+hypergraph H and on its dual H* (four slg_build calls) for the power-law
+Chung-Lu workload (|E| = 1M hyperedges, |V| = 2M vertices, ~21M incidences,
+hyperedge sizes Zipf(2.1) capped at 10^4, vertex weights power law 2.3).
+Throughput is reported in wedges/s, a wedge being one upper-triangle path
+e -> v -> f with |e|, |f| >= s (the exact work of the walk), summed over the
+four builds.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank builds its own independent instance of the
+workload (seed + rank): weak scaling, no collective on the data path.
+``--impl reference`` times the CPU oracle (plain C, all host cores) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "L_s(H) build ms & wedges/s at s=2,8: batched/tiled vs plain GPU kernel, bit-exact"
+UNIT = "wedges/s"
+S_VALUES = (2, 8)
+SIDES = (False, True)
+WORKLOAD = "chung_lu_1m"
+WORKLOAD_TEXT = ("Chung-Lu power-law hypergraph |E|=1M, |V|=2M, ~21M int32 incidences, "
+                 "sizes Zipf(2.1) capped 1e4 (mean ~21), vertex weights power law 2.3; "
+                 "builds L_s(H) and L_s(H*) at s=2 and s=8 per step")
+CPU_SAMPLE_STRIDE = 16      # oracle baseline: every 16th row of each build
+REF_SAMPLE_STRIDE = 64      # --impl reference: every 64th row per step
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--algo", choices=["binned", "plain", "spgemm"], default="binned")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--scale", type=float, default=1.0, help="workload scale (testing)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def aggregate(units: float, ms: float, world: int, device=None):
+    """Whole-job units (sum over ranks) and the slowest rank's time (max)."""
+    if world == 1:
+        return units, ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    m = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    return float(t.item()), float(m.item())
+
+
+def make_workload(rank: int, scale: float):
+    import hypergen
+    c = dict(hypergen.CONFIGS[WORKLOAD])
+    c.pop("kind")
+    c["seed"] = c["seed"] + rank
+    if scale != 1.0:
+        c["m"] = int(c["m"] * scale)
+        c["n"] = int(c["n"] * scale)
+    return hypergen.chung_lu(name=WORKLOAD, **c)
+
+
+def jobs():
+    return [(dual, s) for dual in SIDES for s in S_VALUES]
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", self.gpu_id], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- roofline --
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def walk_bytes(st, b):
+    """Algorithmic bytes of the bin-b walk kernel in one build: per row its
+    list entry, CSR offsets, count and staging offset (24 B); per incidence
+    its column id, tail start and the column's end offset (12 B); per wedge
+    the far end's id (4 B); per pair its staged (j, w) (8 B)."""
+    return (24 * st["rows_bin"][b] + 12 * st["incid_bin"][b] + 4 * st["wedges_bin"][b]
+            + 8 * st["pairs_bin"][b])
+
+
+WALK_KERNELS = ["k_walk_warp", "k_walk_cta<256,2048>", "k_walk_cta<1024,16384>",
+                "k_walk_giant"]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
+    it was taken on the current walk source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    src = os.path.join(ROOT, "paper_2010_11448_gb300", "csrc", "slg_walk.cu")
+    if not os.path.exists(path):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for ln in open(path):
+        kv = dict(x.split("=", 1) for x in ln.split() if "=" in x)
+        if kv.get("kernel") == kernel and kv.get("src_sha") == sha and \
+                kv.get("workload") == WORKLOAD:
+            return float(kv["bytes_per_launch"])
+    return None
+
+
+# ---------------------------------------------------------------- CPU leg --
+
+def cpu_oracle_rate(h, stride: int):
+    """The oracle as it stands, all host cores, every `stride`-th row of each
+    of the four builds; returns (wedges/s, seconds, cores, sample text)."""
+    import numpy as np
+
+    import oracle
+    cores = os.cpu_count() or 1
+    total_w = 0
+    total_t = 0.0
+    for dual, s in jobs():
+        m, n, off, idx = oracle.side(h, dual)
+        rows = np.arange(0, m, stride, dtype=np.int32)
+        t0 = time.perf_counter()
+        oracle.line_graph(m, n, off, idx, s, rows=rows, threads=cores)
+        total_t += (time.perf_counter() - t0) * stride   # extrapolated to all rows
+        total_w += oracle.wedges(m, n, off, idx, s)
+    sample = (f"every {stride}th row of each of the 4 builds (s=2,8 on H and H*); time "
+              f"scaled by {stride} to the full build")
+    return total_w / total_t, total_t / stride, cores, sample
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    h = make_workload(0, args.scale)
+    W = 0
+    import numpy as np
+    sides = {dual: oracle.side(h, dual) for dual in SIDES}
+    for dual, s in jobs():
+        m, n, off, idx = sides[dual]
+        W += oracle.wedges(m, n, off, idx, s)
+    cores = os.cpu_count() or 1
+
+    def step():
+        for dual, s in jobs():
+            m, n, off, idx = sides[dual]
+            rows = np.arange(0, m, REF_SAMPLE_STRIDE, dtype=np.int32)
+            oracle.line_graph(m, n, off, idx, s, rows=rows, threads=cores)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    full_s = dt * REF_SAMPLE_STRIDE / args.steps       # seconds per full step
+    value = W / full_s
+    sample = (f"every {REF_SAMPLE_STRIDE}th row of each of the 4 builds per step; time scaled "
+              f"by {REF_SAMPLE_STRIDE} to the full step")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": full_s * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+           "config": {"workload": WORKLOAD_TEXT, "m": h.m, "n": h.n, "nnz": h.nnz,
+                      "s": list(S_VALUES), "sides": ["H", "H*"]},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- GPU leg --
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import oracle
+    import paper_2010_11448_gb300 as slg
+    from paper_2010_11448_gb300 import build_lib
+    build_lib.build()
+    slg.load()
+
+    h = make_workload(rank, args.scale)
+    dh = slg.to_device(h, dev)
+    algo = args.algo
+    J = jobs()
+    caps, wedges = {}, {}
+    for dual, s in J:
+        caps[(dual, s)] = slg.count(dh, s, dual, algo=algo)
+        wedges[(dual, s)] = slg.wedges(dh, s, dual)
+    outs = {k: slg._outputs(caps[k], False, dev) for k in J}
+    W_step = sum(wedges.values())
+    P_step = sum(caps.values())
+
+    stats_acc = {"launches": 0, "ms_walk": [0.0] * 4, "bytes_walk": [0.0] * 4,
+                 "launch_walk": [0] * 4, "ms_other": 0.0}
+
+    def step(record):
+        for dual, s in J:
+            slg.build(dh, s, dual=dual, algo=algo, out=outs[(dual, s)])
+            if record:
+                st = slg.last_stats()
+                stats_acc["launches"] += st["kernel_launches"]
+                if st["profiled"]:
+                    for b in range(4):
+                        stats_acc["ms_walk"][b] += st["ms_walk"][b]
+                        stats_acc["bytes_walk"][b] += walk_bytes(st, b)
+                        stats_acc["launch_walk"][b] += 1
+                    stats_acc["ms_other"] += st["ms_plan"] + st["ms_scan"] + st["ms_gather"]
+
+    for _ in range(max(args.warmup, 0)):
+        step(False)
+    slg.set_profiling(True)
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = str(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_id) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step(True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    slg.set_profiling(False)
+    ms = e0.elapsed_time(e1)
+    units, ms_max = aggregate(W_step * args.steps, ms, world, dev)
+    value = units / (ms_max / 1e3)
+
+    # roofline of the dominant kernel (largest share of walk time)
+    b = int(np.argmax(stats_acc["ms_walk"]))
+    n_l = max(stats_acc["launch_walk"][b], 1)
+    t_l = stats_acc["ms_walk"][b] / n_l / 1e3
+    bytes_l = stats_acc["bytes_walk"][b] / n_l
+    peak, peak_kind = peaks()
+    achieved = bytes_l / t_l / 1e9 if t_l > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": WALK_KERNELS[b], "achieved": achieved,
+                "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": peak_kind, "traffic": recorded_traffic(WALK_KERNELS[b]),
+                "algorithmic_bytes_per_launch": bytes_l, "ms_per_launch": t_l * 1e3,
+                "walk_ms_share": {WALK_KERNELS[i]: stats_acc["ms_walk"][i] / max(ms, 1e-9)
+                                  for i in range(4)}}
+
+    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+              "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+              "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+              "dtype": "int32", "data": "synthetic",
+              "config": {"workload": WORKLOAD_TEXT, "m": h.m, "n": h.n, "nnz": h.nnz,
+                         "s": list(S_VALUES), "sides": ["H", "H*"], "algo": algo,
+                         "wedges_per_step": W_step, "pairs_per_step": P_step,
+                         "l2": "inputs (CSR+CSC 168 MB) larger than the 129 MB L2; no flush",
+                         "parallelism": f"independent instance per rank x{world}"},
+              "build_ms": None, "roofline": roofline, "clocks": clk.summary(),
+              "gpu_launches": stats_acc["launches"]}
+
+    # per-build ms (one more profiled pass, untimed)
+    per = {}
+    for dual, s in J:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        slg.build(dh, s, dual=dual, algo=algo, out=outs[(dual, s)])
+        per[f"{'H*' if dual else 'H'} s={s}"] = (time.perf_counter() - t0) * 1e3
+    result["build_ms"] = per
+
+    # end to end through the C ABI with host buffers (pinned)
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).pin_memory()
+
+        class HostH:
+            pass
+        hh = HostH()
+        hh.m, hh.n = h.m, h.n
+        hh.e_off, hh.e_idx, hh.v_off, hh.v_idx = (pin(h.e_off), pin(h.e_idx), pin(h.v_off),
+                                                  pin(h.v_idx))
+        houts = {k: tuple(torch.empty(caps[k], dtype=torch.int32).pin_memory()
+                          for _ in range(3)) for k in J}
+
+        def e2e_step():
+            for dual, s in J:
+                slg.build_host(hh, s, dual=dual, algo=algo, out=houts[(dual, s)])
+        e2e_step()
+        torch.cuda.synchronize()
+        k2 = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) * 1e3
+        u2, dt_max = aggregate(W_step * k2, dt, world, dev)
+        in_bytes = 4 * (h.m + 1 + h.n + 1 + 2 * h.nnz)
+        result["e2e"] = {"value": u2 / (dt_max / 1e3), "unit": UNIT,
+                         "h2d_bytes_per_step": in_bytes * len(J),
+                         "d2h_bytes_per_step": 12 * P_step, "steps": k2}
+
+    if rank == 0 and not args.no_cpu:
+        oracle.build()
+        rate, secs, cores, sample = cpu_oracle_rate(h, CPU_SAMPLE_STRIDE)
+        result["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores,
+                                  "kind": "oracle", "sample": sample,
+                                  "seconds": secs}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

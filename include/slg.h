@@ -147,18 +147,30 @@ int slg_build_host(const slg_hypergraph *h, int32_t s, uint32_t flags,
 int slg_wedges(const slg_hypergraph *h, int32_t s, uint32_t flags,
                int64_t *wedges, void *stream);
 
-/* Statistics of the last call made by this host thread. */
+/* Statistics of the last call made by this host thread.  Bins: 0 = warp
+ * (small rows), 1 = CTA small, 2 = CTA large, 3 = giant rows. */
 typedef struct slg_stats {
   int64_t wedges;          /* W_s visited */
   int64_t pairs;           /* |L_s| */
   int64_t rows_active;     /* rows with size >= s */
-  int64_t rows_bin[4];     /* rows per bin: warp, cta-small, cta-large, giant */
+  int64_t rows_bin[4];     /* rows per bin */
   int64_t wedges_bin[4];   /* wedges per bin */
+  int64_t incid_bin[4];    /* CSR incidences of the rows of each bin */
+  int64_t pairs_bin[4];    /* pairs emitted by each bin */
   int32_t kernel_launches; /* kernels launched by the call */
-  int32_t reserved;
+  int32_t profiled;        /* 1 if the ms_* fields below were measured */
+  float ms_plan;           /* validation, maps, filtered CSC, bins */
+  float ms_walk[4];        /* the walk kernel of each bin */
+  float ms_scan;           /* row offsets */
+  float ms_gather;         /* output assembly */
 } slg_stats;
 
 int slg_last_stats(slg_stats *out);
+
+/* Per-phase CUDA-event timing of later calls from this host thread
+ * (enable = 1) or not (0, the default).  Events are recorded on the call's
+ * stream; the times land in slg_stats.ms_*. */
+int slg_set_profiling(int enable);
 
 /* Human-readable text for a status code (static storage). */
 const char *slg_strerror(int status);

@@ -1,0 +1,292 @@
+"""slg: s-line graphs of hypergraphs on one GB300 (sm_103a).
+
+Thin Python binding over the C ABI of ``include/slg.h`` (``libslg.so``).
+It only marshals arguments: every step of the computation runs in the CUDA
+kernels of the library.  There is no CPU fallback; if the compiled library
+is missing the functions raise ``RuntimeError``.
+
+PyTorch supplies device memory and streams.  A hypergraph lives on the
+device as four int32 tensors (CSR e_off/e_idx and CSC v_off/v_idx, see
+``DeviceHypergraph``); results come back as three int32 tensors (i, j, w)
+forming the canonical edge list of L_s (i < j, w >= s, ascending (i, j)).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+__all__ = [
+    "DeviceHypergraph", "to_device", "count", "build", "build_rows",
+    "build_host", "wedges", "last_stats", "set_profiling", "library_path", "load",
+    "SLG_DUAL", "SLG_UNWEIGHTED", "SLG_ALGO_BINNED", "SLG_ALGO_PLAIN",
+    "SLG_ALGO_SPGEMM", "SlgError", "ABI_FUNCTIONS",
+]
+
+SLG_DUAL = 0x1
+SLG_UNWEIGHTED = 0x2
+SLG_ALGO_BINNED = 0x000
+SLG_ALGO_PLAIN = 0x100
+SLG_ALGO_SPGEMM = 0x200
+_ALGOS = {"binned": SLG_ALGO_BINNED, "plain": SLG_ALGO_PLAIN,
+          "spgemm": SLG_ALGO_SPGEMM}
+
+SLG_ERR_CAPACITY = 2
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "_build", "libslg.so")
+
+
+class SlgError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {_strerror(status)} (status {status})")
+
+
+class _Hypergraph(ctypes.Structure):
+    _fields_ = [("n_edges", ctypes.c_int32), ("n_vertices", ctypes.c_int32),
+                ("nnz", ctypes.c_int64), ("e_off", ctypes.c_void_p),
+                ("e_idx", ctypes.c_void_p), ("v_off", ctypes.c_void_p),
+                ("v_idx", ctypes.c_void_p)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("wedges", ctypes.c_int64), ("pairs", ctypes.c_int64),
+                ("rows_active", ctypes.c_int64),
+                ("rows_bin", ctypes.c_int64 * 4),
+                ("wedges_bin", ctypes.c_int64 * 4),
+                ("incid_bin", ctypes.c_int64 * 4),
+                ("pairs_bin", ctypes.c_int64 * 4),
+                ("kernel_launches", ctypes.c_int32),
+                ("profiled", ctypes.c_int32),
+                ("ms_plan", ctypes.c_float),
+                ("ms_walk", ctypes.c_float * 4),
+                ("ms_scan", ctypes.c_float),
+                ("ms_gather", ctypes.c_float)]
+
+
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_VP = ctypes.c_void_p
+_HP = ctypes.POINTER(_Hypergraph)
+
+# name -> (restype, argtypes); every symbol include/slg.h declares.
+ABI_FUNCTIONS = {
+    "slg_count": (ctypes.c_int, [_HP, ctypes.c_int32, ctypes.c_uint32, _I64P, _VP]),
+    "slg_build": (ctypes.c_int, [_HP, ctypes.c_int32, ctypes.c_uint32, _VP, _VP, _VP,
+                                 ctypes.c_int64, _I64P, _VP]),
+    "slg_build_rows": (ctypes.c_int, [_HP, ctypes.c_int32, ctypes.c_uint32,
+                                      ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP,
+                                      ctypes.c_int64, _I64P, _VP]),
+    "slg_build_host": (ctypes.c_int, [_HP, ctypes.c_int32, ctypes.c_uint32, _VP, _VP,
+                                      _VP, ctypes.c_int64, _I64P, _VP]),
+    "slg_wedges": (ctypes.c_int, [_HP, ctypes.c_int32, ctypes.c_uint32, _I64P, _VP]),
+    "slg_last_stats": (ctypes.c_int, [ctypes.POINTER(_Stats)]),
+    "slg_set_profiling": (ctypes.c_int, [ctypes.c_int]),
+    "slg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "slg_abi_version": (ctypes.c_int, []),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str | None = None):
+    """Load libslg.so (raises RuntimeError if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or library_path()
+        if not os.path.exists(p):
+            raise RuntimeError(
+                f"slg CUDA library not found at {p}; build it with "
+                "paper_2010_11448_gb300.build_lib.build() (no CPU fallback exists)")
+        lib = ctypes.CDLL(p)
+        for name, (res, args) in ABI_FUNCTIONS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def _strerror(status: int) -> str:
+    try:
+        return load().slg_strerror(status).decode()
+    except Exception:  # pragma: no cover - library missing
+        return "unknown"
+
+
+class DeviceHypergraph:
+    """CSR + CSC of H as int32 CUDA tensors (caller-owned device memory)."""
+
+    def __init__(self, m, n, e_off, e_idx, v_off, v_idx):
+        self.m, self.n = int(m), int(n)
+        self.e_off, self.e_idx, self.v_off, self.v_idx = e_off, e_idx, v_off, v_idx
+        self.nnz = int(e_idx.shape[0])
+        self._s = _Hypergraph(self.m, self.n, self.nnz, e_off.data_ptr(),
+                              e_idx.data_ptr() if self.nnz else 0, v_off.data_ptr(),
+                              v_idx.data_ptr() if self.nnz else 0)
+
+    @property
+    def struct(self):
+        return self._s
+
+    def rows(self, dual: bool) -> int:
+        return self.n if dual else self.m
+
+
+def to_device(h, device="cuda") -> DeviceHypergraph:
+    """Copy a host hypergraph (any object with m, n, e_off, e_idx, v_off,
+    v_idx numpy arrays) to the device."""
+    import torch
+
+    def t(a):
+        a = np.ascontiguousarray(a, dtype=np.int32)
+        if a.shape[0] == 0:
+            return torch.zeros(1, dtype=torch.int32, device=device)[:0]
+        return torch.from_numpy(a).to(device)
+
+    return DeviceHypergraph(h.m, h.n, t(h.e_off), t(h.e_idx), t(h.v_off), t(h.v_idx))
+
+
+def _flags(dual, unweighted, algo):
+    f = _ALGOS[algo]
+    if dual:
+        f |= SLG_DUAL
+    if unweighted:
+        f |= SLG_UNWEIGHTED
+    return f
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def count(h: DeviceHypergraph, s: int, dual=False, unweighted=False,
+          algo="binned", stream=None) -> int:
+    """|L_s(H)| (or of H* with dual=True)."""
+    n = ctypes.c_int64(0)
+    rc = load().slg_count(ctypes.byref(h.struct), int(s), _flags(dual, unweighted, algo),
+                          ctypes.byref(n), _stream(stream))
+    if rc != 0:
+        raise SlgError(rc, "slg_count")
+    return int(n.value)
+
+
+def _outputs(capacity, unweighted, device):
+    import torch
+    cap = max(int(capacity), 1)
+    oi = torch.empty(cap, dtype=torch.int32, device=device)
+    oj = torch.empty(cap, dtype=torch.int32, device=device)
+    ow = None if unweighted else torch.empty(cap, dtype=torch.int32, device=device)
+    return oi, oj, ow
+
+
+def build(h: DeviceHypergraph, s: int, dual=False, unweighted=False,
+          algo="binned", capacity=None, out=None, stream=None):
+    """The canonical edge list of L_s as int32 tensors (i, j, w); w is None
+    with unweighted=True.  Without ``capacity``/``out`` the pair count is
+    taken first with ``count`` (an extra walk)."""
+    flags = _flags(dual, unweighted, algo)
+    if out is None:
+        if capacity is None:
+            capacity = count(h, s, dual, unweighted, algo, stream)
+        out = _outputs(capacity, unweighted, h.e_off.device)
+    oi, oj, ow = out
+    cap = int(oi.shape[0])
+    n = ctypes.c_int64(0)
+    rc = load().slg_build(ctypes.byref(h.struct), int(s), flags, oi.data_ptr(),
+                          oj.data_ptr(), ow.data_ptr() if ow is not None else None,
+                          cap, ctypes.byref(n), _stream(stream))
+    if rc != 0:
+        raise SlgError(rc, "slg_build")
+    p = int(n.value)
+    return oi[:p], oj[:p], (ow[:p] if ow is not None else None)
+
+
+def build_rows(h: DeviceHypergraph, s: int, row_begin: int, row_end: int,
+               dual=False, unweighted=False, algo="binned", capacity=0,
+               out=None, stream=None):
+    """Rows [row_begin, row_end) of the edge list.  Returns (i, j, w) or
+    raises SlgError with status 2 (capacity) carrying the needed count in
+    ``.needed``."""
+    flags = _flags(dual, unweighted, algo)
+    if out is None:
+        out = _outputs(capacity, unweighted, h.e_off.device)
+    oi, oj, ow = out
+    n = ctypes.c_int64(0)
+    rc = load().slg_build_rows(ctypes.byref(h.struct), int(s), flags, int(row_begin),
+                               int(row_end), oi.data_ptr(), oj.data_ptr(),
+                               ow.data_ptr() if ow is not None else None,
+                               int(oi.shape[0]) if capacity else 0, ctypes.byref(n),
+                               _stream(stream))
+    if rc != 0:
+        err = SlgError(rc, "slg_build_rows")
+        err.needed = int(n.value)
+        raise err
+    p = int(n.value)
+    return oi[:p], oj[:p], (ow[:p] if ow is not None else None)
+
+
+def build_host(h, s: int, dual=False, unweighted=False, algo="binned",
+               capacity: int = 0, out=None, stream=None):
+    """End-to-end from host arrays: ``h`` holds numpy (ideally pinned torch
+    CPU) int32 arrays; the library copies them in, builds, copies back.
+    ``out`` = three host int32 arrays of the same capacity."""
+    def ptr(a):
+        if hasattr(a, "data_ptr"):
+            return a.data_ptr()
+        return a.ctypes.data
+    st = _Hypergraph(int(h.m), int(h.n), int(h.e_idx.shape[0]), ptr(h.e_off),
+                     ptr(h.e_idx), ptr(h.v_off), ptr(h.v_idx))
+    if out is None:
+        cap = max(int(capacity), 1)
+        out = (np.empty(cap, np.int32), np.empty(cap, np.int32),
+               None if unweighted else np.empty(cap, np.int32))
+    oi, oj, ow = out
+    n = ctypes.c_int64(0)
+    rc = load().slg_build_host(ctypes.byref(st), int(s), _flags(dual, unweighted, algo),
+                               ptr(oi), ptr(oj), ptr(ow) if ow is not None else None,
+                               int(oi.shape[0]), ctypes.byref(n), _stream(stream))
+    if rc != 0:
+        err = SlgError(rc, "slg_build_host")
+        err.needed = int(n.value)
+        raise err
+    p = int(n.value)
+    return oi[:p], oj[:p], (ow[:p] if ow is not None else None)
+
+
+def wedges(h: DeviceHypergraph, s: int, dual=False, stream=None) -> int:
+    """W_s: the upper-triangle wedges the walk visits after the size filter."""
+    n = ctypes.c_int64(0)
+    rc = load().slg_wedges(ctypes.byref(h.struct), int(s), _flags(dual, False, "binned"),
+                           ctypes.byref(n), _stream(stream))
+    if rc != 0:
+        raise SlgError(rc, "slg_wedges")
+    return int(n.value)
+
+
+def last_stats() -> dict:
+    st = _Stats()
+    load().slg_last_stats(ctypes.byref(st))
+    return {"wedges": st.wedges, "pairs": st.pairs, "rows_active": st.rows_active,
+            "rows_bin": list(st.rows_bin), "wedges_bin": list(st.wedges_bin),
+            "incid_bin": list(st.incid_bin), "pairs_bin": list(st.pairs_bin),
+            "kernel_launches": st.kernel_launches, "profiled": bool(st.profiled),
+            "ms_plan": st.ms_plan, "ms_walk": list(st.ms_walk), "ms_scan": st.ms_scan,
+            "ms_gather": st.ms_gather}
+
+
+def set_profiling(enable: bool) -> None:
+    """Per-phase CUDA-event timing of later calls on this thread."""
+    load().slg_set_profiling(1 if enable else 0)

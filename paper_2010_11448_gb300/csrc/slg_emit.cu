@@ -1,0 +1,130 @@
+// Output assembly: the exclusive scan of the per-row pair counts gives every
+// row its place in the canonical (i, j)-ordered edge list (rows in ascending
+// i, each row's pairs already in ascending j), and the gather copies the
+// staged rows there.  This replaces the paper's concatenation of thread-local
+// edge vectors (Section IV-F) with a deterministic layout.
+#include "slg_internal.cuh"
+
+namespace slg {
+
+namespace {
+
+constexpr int kNT = 256;
+constexpr int kIPT = 16;
+constexpr int kTile = kNT * kIPT;
+
+__global__ __launch_bounds__(kNT) void k_rowscan_reduce(const int32_t *__restrict__ n_e,
+                                                        int32_t rows, long long *__restrict__ tile,
+                                                        const Meta *meta) {
+  if (meta->err) return;
+  __shared__ long long ws[kNT / 32 + 1];
+  const int64_t base = (int64_t)blockIdx.x * kTile;
+  long long c = 0;
+  for (int i = 0; i < kIPT; ++i) {
+    const int64_t r = base + (int64_t)i * kNT + threadIdx.x;
+    if (r < rows) c += n_e[r];
+  }
+  long long total;
+  block_inclusive_scan64<kNT>(c, ws, &total);
+  if (threadIdx.x == 0) tile[blockIdx.x] = total;
+}
+
+__global__ __launch_bounds__(1024) void k_scan_tiles64(long long *tile, int32_t n, Meta *meta) {
+  if (meta->err) return;
+  __shared__ long long ws[1024 / 32 + 1];
+  __shared__ long long carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int32_t base = 0; base < n; base += 1024) {
+    const int32_t i = base + threadIdx.x;
+    const long long x = i < n ? tile[i] : 0;
+    long long total;
+    const long long inc = block_inclusive_scan64<1024>(x, ws, &total);
+    if (i < n) tile[i] = carry + inc - x;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    tile[n] = carry;
+    meta->pairs = (unsigned long long)carry;
+  }
+}
+
+__global__ __launch_bounds__(kNT) void k_rowscan_apply(const int32_t *__restrict__ n_e, int32_t rows,
+                                                       const long long *__restrict__ tile,
+                                                       long long *__restrict__ row_ptr,
+                                                       int32_t ntiles, const Meta *meta) {
+  if (meta->err) return;
+  __shared__ long long ws[kNT / 32 + 1];
+  const int64_t base = (int64_t)blockIdx.x * kTile;
+  long long carry = tile[blockIdx.x];
+  for (int i = 0; i < kIPT; ++i) {
+    const int64_t r = base + (int64_t)i * kNT + threadIdx.x;
+    const long long x = r < rows ? n_e[r] : 0;
+    long long total;
+    const long long inc = block_inclusive_scan64<kNT>(x, ws, &total);
+    if (r < rows) row_ptr[r] = carry + inc - x;
+    carry += total;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) row_ptr[rows] = tile[ntiles];
+}
+
+constexpr int kGatherRows = 256;
+
+// A block owns kGatherRows consecutive rows and copies their staged pairs to
+// the output range [row_ptr[r0], row_ptr[r0 + rows)), each thread finding its
+// row by binary search over the block's offsets.
+__global__ __launch_bounds__(kNT) void k_gather(int32_t row_begin, int32_t rows,
+                                                const long long *__restrict__ row_ptr,
+                                                const long long *__restrict__ stage_pos,
+                                                const int32_t *__restrict__ stage_j,
+                                                const int32_t *__restrict__ stage_w,
+                                                int32_t *__restrict__ out_i,
+                                                int32_t *__restrict__ out_j,
+                                                int32_t *__restrict__ out_w, int unweighted,
+                                                const Meta *meta) {
+  if (meta->err) return;
+  __shared__ long long s_ptr[kGatherRows + 1];
+  __shared__ long long s_sp[kGatherRows];
+  const int32_t r0 = blockIdx.x * kGatherRows;
+  const int32_t nr = min(kGatherRows, rows - r0);
+  for (int i = threadIdx.x; i <= nr; i += kNT) s_ptr[i] = row_ptr[r0 + i];
+  for (int i = threadIdx.x; i < nr; i += kNT) s_sp[i] = stage_pos[r0 + i];
+  __syncthreads();
+  const long long p1 = s_ptr[nr];
+  for (long long p = s_ptr[0] + threadIdx.x; p < p1; p += kNT) {
+    int lo = 0, hi = nr;  // s_ptr[lo] <= p < s_ptr[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (s_ptr[mid] <= p) lo = mid;
+      else hi = mid;
+    }
+    const long long src = s_sp[lo] + (p - s_ptr[lo]);
+    out_i[p] = row_begin + r0 + lo;
+    out_j[p] = stage_j[src];
+    if (!unweighted) out_w[p] = stage_w[src];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_row_scan(int32_t rows, const Work &w, cudaStream_t st) {
+  const int32_t ntiles = (rows + kTile - 1) / kTile;
+  if (ntiles > 0) k_rowscan_reduce<<<ntiles, kNT, 0, st>>>(w.n_e, rows, w.tile64, w.meta);
+  k_scan_tiles64<<<1, 1024, 0, st>>>(w.tile64, ntiles, w.meta);
+  if (ntiles > 0)
+    k_rowscan_apply<<<ntiles, kNT, 0, st>>>(w.n_e, rows, w.tile64, w.row_ptr, ntiles, w.meta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather(int32_t row_begin, int32_t rows, const Work &w, int32_t *out_i,
+                          int32_t *out_j, int32_t *out_w, int unweighted, cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  const int grid = (rows + kGatherRows - 1) / kGatherRows;
+  k_gather<<<grid, kNT, 0, st>>>(row_begin, rows, w.row_ptr, w.stage_pos, w.stage_j, w.stage_w,
+                                 out_i, out_j, out_w, unweighted, w.meta);
+  return cudaGetLastError();
+}
+
+}  // namespace slg

@@ -1,0 +1,303 @@
+// Internal declarations of the slg CUDA library (not part of the C ABI).
+//
+// Terminology.  The side being computed (H, or H* with SLG_DUAL) has R rows
+// (its hyperedges) and C columns (its vertices).  CSR = (r_off, r_idx) lists
+// the columns of every row, CSC = (c_off, c_idx) the rows of every column;
+// both strictly ascending.  A wedge is a path e -> v -> f with v in e and f in
+// N(v) (Section IV-B, the two inner loops of Algorithm 2).  Only wedges with
+// f > e are walked (the strict upper triangle of Algorithm 3) and only rows
+// with |row| >= s take part (degree-based pruning of Algorithm 3).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/slg.h"
+
+namespace slg {
+
+constexpr int kWarp = 32;
+constexpr int32_t kEmpty = -1;
+
+// Row bins by wedge work (the degree-binned scheduler).
+enum Bin : int { kBinWarp = 0, kBinCtaS = 1, kBinCtaL = 2, kBinGiant = 3, kNumBins = 4 };
+
+// Upper bounds on a row's wedge count for each non-giant bin.  The hash tables
+// hold twice the bound, so a row can never fill its table (distinct
+// neighbours <= wedges).
+constexpr int32_t kWarpMaxWork = 128;
+constexpr int32_t kCtaSMaxWork = 1024;
+constexpr int32_t kCtaLMaxWork = 8192;
+
+// Counters the device writes and the host reads once per call.
+struct Meta {
+  int32_t err;                         // first slg_status raised on the device
+  int32_t err_where;                   // which check raised it
+  unsigned long long rows_bin[kNumBins];
+  unsigned long long wedges_bin[kNumBins];
+  unsigned long long incid_bin[kNumBins];
+  unsigned long long pairs_bin[kNumBins];
+  unsigned long long wedges;           // W_s
+  unsigned long long active;           // rows with size >= s in range
+  unsigned long long pairs;            // |L_s| over the row range
+  unsigned long long stage_cursor;     // staging allocator
+  unsigned long long stage_overflow;   // rows that did not fit the staging
+  unsigned int giant_ticket;           // dynamic giant-row scheduling
+  int32_t kept;                        // entries of the filtered CSC
+};
+
+// Where a device-side check fired (for error reports).
+enum Where : int32_t {
+  kWhereNone = 0, kWhereRowOffsets = 1, kWhereRowIds = 2, kWhereColOffsets = 3,
+  kWhereColIds = 4, kWhereMismatch = 5, kWhereHash = 6, kWhereGiant = 7,
+};
+
+__device__ __forceinline__ void raise_error(Meta *meta, int32_t status, int32_t where) {
+  if (atomicCAS(&meta->err, 0, status) == 0) meta->err_where = where;
+}
+
+// ------------------------------------------------------------------ scans --
+
+__device__ __forceinline__ int32_t warp_inclusive_scan(int32_t x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    int32_t y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  return x;
+}
+
+__device__ __forceinline__ long long warp_inclusive_scan64(long long x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    long long y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  return x;
+}
+
+// Block-wide inclusive scan; `ws` is shared scratch of NT/32 + 1 ints.
+// Returns the thread's inclusive prefix, writes the block total to *total.
+template <int NT>
+__device__ __forceinline__ int32_t block_inclusive_scan(int32_t x, int32_t *ws,
+                                                        int32_t *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = NT / 32;
+  int32_t inc = warp_inclusive_scan(x);
+  if (lane == 31) ws[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    int32_t v = lane < NW ? ws[lane] : 0;
+    int32_t vi = warp_inclusive_scan(v);
+    if (lane < NW) ws[lane] = vi - v;  // exclusive warp offsets
+    if (lane == NW - 1) ws[NW] = vi;
+  }
+  __syncthreads();
+  inc += ws[warp];
+  *total = ws[NW];
+  __syncthreads();  // ws may be reused right after
+  return inc;
+}
+
+template <int NT>
+__device__ __forceinline__ long long block_inclusive_scan64(long long x, long long *ws,
+                                                            long long *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = NT / 32;
+  long long inc = warp_inclusive_scan64(x);
+  if (lane == 31) ws[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    long long v = lane < NW ? ws[lane] : 0;
+    long long vi = warp_inclusive_scan64(v);
+    if (lane < NW) ws[lane] = vi - v;
+    if (lane == NW - 1) ws[NW] = vi;
+  }
+  __syncthreads();
+  inc += ws[warp];
+  *total = ws[NW];
+  __syncthreads();
+  return inc;
+}
+
+// Position of `key` in the ascending array a[lo, hi), or -1.
+__device__ __forceinline__ int32_t find_sorted(const int32_t *__restrict__ a, int32_t lo,
+                                               int32_t hi, int32_t key) {
+  while (lo < hi) {
+    int32_t mid = lo + ((hi - lo) >> 1);
+    int32_t x = __ldg(a + mid);
+    if (x < key) lo = mid + 1;
+    else if (x > key) hi = mid;
+    else return mid;
+  }
+  return -1;
+}
+
+// Multiplicative hash onto [0, T) (Fibonacci hashing + fast range).
+__device__ __forceinline__ uint32_t hash_slot(int32_t f, uint32_t T) {
+  return __umulhi((uint32_t)f * 0x9E3779B1u, T);
+}
+
+// --------------------------------------------------------- wedge walking --
+//
+// The rows's incidences k in [k0, k1) each own a "tail": the entries after the
+// row in the filtered CSC of their column, c_idx_s[tail_beg[k], c_off_s[v+1]).
+// The union of the tails (as a multiset) is the row's wedge list.  The walkers
+// below flatten the tails and hand every wedge's far end f to `fn`, with the
+// work of a batch spread evenly over the threads (load-balanced search over
+// the prefix sums of the tail lengths) and coalesced reads of c_idx_s.
+
+struct Walk {
+  const int32_t *r_off, *r_idx;      // CSR of the side
+  const int32_t *c_off_s, *c_idx_s;  // CSC filtered to rows of size >= s
+  const int32_t *tail_beg;           // per CSR incidence of an active row
+};
+
+// CTA-wide walker.  Shared scratch: s_beg[NT], s_pref[NT + 1], ws[NT/32 + 1].
+template <int NT, int G, class Fn>
+__device__ __forceinline__ void cta_walk(const Walk &w, int32_t k0, int32_t k1,
+                                         int32_t *s_beg, int32_t *s_pref, int32_t *ws,
+                                         Fn &&fn) {
+  for (int32_t base = k0; base < k1; base += NT) {
+    const int32_t k = base + (int32_t)threadIdx.x;
+    int32_t b = 0, len = 0;
+    if (k < k1) {
+      const int32_t v = __ldg(w.r_idx + k);
+      b = __ldg(w.tail_beg + k);
+      len = __ldg(w.c_off_s + v + 1) - b;
+    }
+    int32_t total;
+    const int32_t inc = block_inclusive_scan<NT>(len, ws, &total);
+    s_beg[threadIdx.x] = b;
+    s_pref[threadIdx.x + 1] = inc;
+    if (threadIdx.x == 0) s_pref[0] = 0;
+    __syncthreads();
+    for (int32_t i0 = (int32_t)threadIdx.x * G; i0 < total; i0 += NT * G) {
+      int32_t lo = 0, hi = NT;  // invariant: s_pref[lo] <= i0 < s_pref[hi]
+      while (hi - lo > 1) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (s_pref[mid] <= i0) lo = mid;
+        else hi = mid;
+      }
+      int32_t j = lo;
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int32_t i = i0 + g;
+        if (i < total) {
+          while (s_pref[j + 1] <= i) ++j;
+          fn(__ldg(w.c_idx_s + s_beg[j] + (i - s_pref[j])));
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Warp-wide walker for small rows (no shared memory; shuffles only).
+template <class Fn>
+__device__ __forceinline__ void warp_walk(const Walk &w, int32_t k0, int32_t k1, Fn &&fn) {
+  const int lane = threadIdx.x & 31;
+  for (int32_t base = k0; base < k1; base += 32) {
+    const int32_t k = base + lane;
+    int32_t b = 0, len = 0;
+    if (k < k1) {
+      const int32_t v = __ldg(w.r_idx + k);
+      b = __ldg(w.tail_beg + k);
+      len = __ldg(w.c_off_s + v + 1) - b;
+    }
+    const int32_t inc = warp_inclusive_scan(len);
+    const int32_t total = __shfl_sync(0xffffffffu, inc, 31);
+    for (int32_t i0 = 0; i0 < total; i0 += 32) {
+      const int32_t i = i0 + lane;
+      // j = number of incidences whose tail ends at or before i
+      int32_t j = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int32_t cand = j + step;
+        const int32_t end = __shfl_sync(0xffffffffu, inc, cand - 1);
+        if (end <= i) j = cand;
+      }
+      const int32_t jj = j < 31 ? j : 31;
+      const int32_t seg_inc = __shfl_sync(0xffffffffu, inc, jj);
+      const int32_t seg_len = __shfl_sync(0xffffffffu, len, jj);
+      const int32_t seg_beg = __shfl_sync(0xffffffffu, b, jj);
+      if (i < total) fn(__ldg(w.c_idx_s + seg_beg + (i - (seg_inc - seg_len))));
+    }
+  }
+}
+
+// ------------------------------------------------------------- launchers --
+// All launchers enqueue on `st` and return the first CUDA error, if any.
+
+struct Side {
+  int32_t R, C;     // rows (hyperedges of the side), columns (its vertices)
+  int64_t nnz;
+  const int32_t *r_off, *r_idx, *c_off, *c_idx;
+};
+
+// Per-call device buffers (carved out of one pool allocation).
+struct Work {
+  int32_t *csr2csc;    // [nnz] CSC position of every CSR incidence
+  int32_t *qs;         // [nnz + 1] exclusive scan of "row of this CSC entry kept"
+  int32_t *c_idx_s;    // [nnz] filtered CSC ids
+  int32_t *c_off_s;    // [C + 1] filtered CSC offsets
+  int32_t *tail_beg;   // [nnz]
+  int32_t *tile;       // [ntiles + 1] scan scratch
+  int32_t *bin_rows;   // [kNumBins][R] row lists
+  int32_t *n_e;        // [R] pairs per row
+  long long *stage_pos;// [R] staging offset per row, -1 = not staged
+  long long *row_ptr;  // [R + 1] output offsets (relative to row_begin)
+  long long *tile64;   // [ntiles64 + 1]
+  int32_t *stage_j, *stage_w;  // [stage_cap]
+  long long stage_cap;
+  Meta *meta;
+};
+
+cudaError_t launch_validate(const Side &s, Meta *meta, cudaStream_t st);
+cudaError_t launch_csr2csc(const Side &s, int32_t *csr2csc, Meta *meta, cudaStream_t st);
+cudaError_t launch_filter(const Side &s, int32_t smin, const Work &w, cudaStream_t st);
+cudaError_t launch_rows_work(const Side &s, int32_t smin, int32_t row_begin, int32_t row_end,
+                             const Work &w, cudaStream_t st);
+// Output modes of the walk: COUNT (pairs per row only), STAGE (each row's
+// sorted pairs appended to a staging area at an atomically reserved offset),
+// DIRECT (written to their final place; row_ptr known).
+enum Mode : int { kCount = 0, kStage = 1, kDirect = 2 };
+
+struct EmitArgs {
+  int mode;
+  int unweighted;
+  int32_t smin;
+  int32_t row_begin;
+  int32_t *n_e;                       // [rows] pairs per row
+  long long *stage_pos;               // [rows] staging offset, -1 = none
+  int32_t *stage_j, *stage_w;         // STAGE
+  long long stage_cap;
+  const long long *row_ptr;           // DIRECT
+  int32_t *out_i, *out_j, *out_w;     // DIRECT
+  Meta *meta;
+};
+
+struct WalkLaunch {
+  Walk w;
+  EmitArgs a;
+  const int32_t *bin_rows;  // [kNumBins][rows] row lists
+  int32_t rows;             // rows in the range (list stride)
+  int32_t *giant_scratch;   // [giant_ctas][R_pad] zero-initialised counters
+  int32_t giant_ctas;
+  int32_t R_pad;            // R rounded up to a multiple of 1024
+};
+
+// ev (optional): kNumBins + 1 events recorded before the first and after
+// every bin kernel.
+cudaError_t launch_walk(const WalkLaunch &L, cudaStream_t st, int32_t *launches,
+                        cudaEvent_t *ev = nullptr);
+cudaError_t launch_row_scan(int32_t rows, const Work &w, cudaStream_t st);
+cudaError_t launch_gather(int32_t row_begin, int32_t rows, const Work &w, int32_t *out_i,
+                          int32_t *out_j, int32_t *out_w, int unweighted, cudaStream_t st);
+
+int giant_ctas_for_device();
+size_t giant_smem_bytes(int32_t R);
+
+}  // namespace slg

@@ -1,0 +1,256 @@
+"""CUDA path vs the CPU oracle, element by element (bit-exact: every count is
+an exact integer).  All calls go through the C ABI via the thin binding."""
+import numpy as np
+import pytest
+
+import hypergen as hg
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+slg = pytest.importorskip("paper_2010_11448_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2010_11448_gb300 import build_lib
+    build_lib.build()
+    slg.load()
+
+
+def as_np(t):
+    i, j, w = t
+    cols = [i.cpu().numpy(), j.cpu().numpy()]
+    cols.append(w.cpu().numpy() if w is not None else np.zeros_like(cols[0]))
+    return np.stack(cols, 1).astype(np.int64) if cols[0].shape[0] else np.zeros((0, 3), np.int64)
+
+
+def gpu_lg(dh, s, dual=False, **kw):
+    return as_np(slg.build(dh, s, dual=dual, **kw))
+
+
+def want_lg(h, s, dual=False, rows=None, threads=8):
+    return oracle.canonical(*oracle.line_graph_of(h, s, dual=dual, rows=rows, threads=threads))
+
+
+# ------------------------------------------------------------- small cases --
+
+@pytest.mark.parametrize("dual", [False, True])
+@pytest.mark.parametrize("s", [1, 2, 3])
+def test_uniform_2k(dual, s):
+    h = hg.config("uniform_2k")
+    dh = slg.to_device(h)
+    assert np.array_equal(gpu_lg(dh, s, dual), want_lg(h, s, dual))
+
+
+def test_random_small_edge_cases():
+    # empty rows, singletons, duplicated rows, isolated vertices
+    for seed in range(40):
+        h = hg.random_small(seed)
+        dh = slg.to_device(h)
+        for dual in (False, True):
+            for s in (1, 2, 3):
+                got = gpu_lg(dh, s, dual)
+                assert np.array_equal(got, want_lg(h, s, dual)), (seed, dual, s)
+
+
+def test_fig1():
+    import pins
+    names, rows, facts = pins.load_fig1()
+    h = hg.from_rows(rows, 12)
+    dh = slg.to_device(h)
+    for dual in (False, True):
+        for s in (1, 2, 3):
+            assert np.array_equal(gpu_lg(dh, s, dual), want_lg(h, s, dual))
+
+
+def test_degenerate_inputs():
+    # no incidences at all, s above every size, a single hyperedge
+    for h in (hg.from_rows([[], [], []], 5), hg.from_rows([[0, 1, 2]], 3),
+              hg.from_rows([[0, 1], [0, 1]], 2)):
+        dh = slg.to_device(h)
+        for dual in (False, True):
+            for s in (1, 2, 3, 100):
+                assert np.array_equal(gpu_lg(dh, s, dual), want_lg(h, s, dual))
+                assert slg.count(dh, s, dual) == want_lg(h, s, dual).shape[0]
+
+
+def test_graph_special_case():
+    rng = np.random.default_rng(3)
+    edges = sorted({tuple(sorted(rng.choice(300, 2, replace=False).tolist()))
+                    for _ in range(2000)})
+    h = hg.graph(300, edges)
+    dh = slg.to_device(h)
+    for dual in (False, True):
+        for s in (1, 2):
+            assert np.array_equal(gpu_lg(dh, s, dual), want_lg(h, s, dual))
+
+
+# --------------------------------------- medium: every bin incl. giant rows --
+
+@pytest.fixture(scope="module")
+def medium():
+    # Sizes capped at 3000 with mean 20: rows reach every bin, including the
+    # giant one (work > 8192) on both sides.
+    h = hg.chung_lu(30_000, 60_000, seed=21, size_cap=3000)
+    return h, slg.to_device(h)
+
+
+@pytest.mark.parametrize("dual", [False, True])
+@pytest.mark.parametrize("s", [1, 2, 4, 8, 16])
+def test_medium_all_bins(medium, dual, s):
+    h, dh = medium
+    got = gpu_lg(dh, s, dual)
+    assert np.array_equal(got, want_lg(h, s, dual))
+    st = slg.last_stats()
+    m, n, off, idx = oracle.side(h, dual)
+    assert st["wedges"] == oracle.wedges(m, n, off, idx, s)
+    if s <= 4:
+        assert st["rows_bin"][3] > 0, "giant bin not exercised"
+
+
+def test_medium_unweighted_same_pairs(medium):
+    h, dh = medium
+    for dual in (False, True):
+        for s in (2, 8):
+            a = gpu_lg(dh, s, dual)
+            b = gpu_lg(dh, s, dual, unweighted=True)
+            assert np.array_equal(a[:, :2], b[:, :2])
+
+
+def test_medium_count_and_wedges(medium):
+    h, dh = medium
+    for dual in (False, True):
+        m, n, off, idx = oracle.side(h, dual)
+        for s in (1, 3, 9):
+            assert slg.count(dh, s, dual) == want_lg(h, s, dual).shape[0]
+            assert slg.wedges(dh, s, dual) == oracle.wedges(m, n, off, idx, s)
+
+
+def test_medium_row_ranges_concatenate(medium):
+    h, dh = medium
+    s = 2
+    full = want_lg(h, s)
+    parts = []
+    bounds = [0, 7, 1000, 1001, 17_000, h.m]
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        try:
+            parts.append(as_np(slg.build_rows(dh, s, a, b, capacity=0)))
+        except slg.SlgError as exc:
+            assert exc.status == 2
+            parts.append(as_np(slg.build_rows(dh, s, a, b, capacity=max(exc.needed, 1))))
+    assert np.array_equal(np.concatenate(parts), full)
+
+
+def test_capacity_error_reports_count(medium):
+    h, dh = medium
+    n = slg.count(dh, 3)
+    with pytest.raises(slg.SlgError) as ei:
+        slg.build(dh, 3, capacity=max(n - 1, 1))
+    assert ei.value.status == 2
+
+
+def test_small_staging_falls_back_to_direct(medium):
+    # A capacity equal to the count makes staging exact; the result must be
+    # identical whichever emission path ran.
+    h, dh = medium
+    n = slg.count(dh, 2, True)
+    got = as_np(slg.build(dh, 2, dual=True, capacity=n))
+    assert np.array_equal(got, want_lg(h, 2, True))
+
+
+def test_host_entry_point(medium):
+    h, _ = medium
+    want = want_lg(h, 4)
+    got = slg.build_host(h, 4, capacity=want.shape[0] + 5)
+    assert np.array_equal(np.stack([a for a in got], 1).astype(np.int64), want)
+
+
+def test_on_side_stream(medium):
+    h, dh = medium
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        got = gpu_lg(dh, 4, stream=st)
+    st.synchronize()
+    assert np.array_equal(got, want_lg(h, 4))
+
+
+# ------------------------------------------------------------ bad inputs --
+
+def _corrupt(h, what):
+    e_off, e_idx = h.e_off.copy(), h.e_idx.copy()
+    v_off, v_idx = h.v_off.copy(), h.v_idx.copy()
+    if what == "unsorted_row":
+        k = int(np.argmax(np.diff(e_off) >= 3))
+        a = e_off[k]
+        e_idx[a], e_idx[a + 1] = e_idx[a + 1], e_idx[a]
+    elif what == "id_out_of_range":
+        e_idx[0] = h.n + 5
+    elif what == "offset_beyond_nnz":
+        e_off[-1] = e_off[-1] + 10
+    elif what == "csc_mismatch":
+        v_idx = v_idx.copy()
+        v_idx[0] = (v_idx[0] + 1) % h.m
+        v_idx[: v_off[1]] = np.sort(v_idx[: v_off[1]])
+    return hg.Hypergraph(h.m, h.n, e_off, e_idx, v_off, v_idx)
+
+
+@pytest.mark.parametrize("what", ["unsorted_row", "id_out_of_range",
+                                  "offset_beyond_nnz", "csc_mismatch"])
+def test_malformed_input_is_an_error_status(what):
+    h = hg.uniform(500, 800, 3, 12, seed=2)
+    bad = _corrupt(h, what)
+    dh = slg.to_device(bad)
+    with pytest.raises(slg.SlgError) as ei:
+        slg.count(dh, 2)
+    assert ei.value.status == 1
+    # the library stays usable afterwards
+    good = slg.to_device(h)
+    assert np.array_equal(gpu_lg(good, 2), want_lg(h, 2))
+
+
+def test_bad_arguments():
+    h = hg.uniform(50, 80, 1, 5, seed=2)
+    dh = slg.to_device(h)
+    for s in (0, -3):
+        with pytest.raises(slg.SlgError) as ei:
+            slg.count(dh, s)
+        assert ei.value.status == 1
+
+
+# ---------------------------------------------- full size, sampled outputs --
+
+@pytest.fixture(scope="module")
+def chung_lu_1m():
+    h = hg.config("chung_lu_1m")
+    return h, slg.to_device(h)
+
+
+@pytest.mark.parametrize("dual", [False, True])
+@pytest.mark.parametrize("s", [2, 8])
+def test_chung_lu_1m_sampled_rows(chung_lu_1m, dual, s):
+    """Full-size workload in the benchmark's launch configuration; every
+    97th row (plus the rows of the largest hyperedges) compared with the
+    oracle, and order / threshold / size-filter properties checked on all
+    pairs (on the device: the output has up to ~5e8 pairs)."""
+    h, dh = chung_lu_1m
+    i, j, w = slg.build(dh, s, dual=dual)
+    m, n, off, idx = oracle.side(h, dual)
+    sizes_np = np.diff(off)
+    heavy = np.argsort(sizes_np)[-64:]
+    rows = np.unique(np.concatenate([np.arange(0, m, 97), heavy])).astype(np.int32)
+    want = oracle.canonical(*oracle.line_graph(m, n, off, idx, s, rows=rows, threads=16))
+    sel = torch.isin(i, torch.from_numpy(rows).to(i.device))
+    got = np.stack([i[sel].cpu().numpy(), j[sel].cpu().numpy(), w[sel].cpu().numpy()],
+                   1).astype(np.int64)
+    assert np.array_equal(got, want)
+    # properties of every pair, checked on the device
+    assert bool(torch.all(i < j)) and bool(torch.all(w >= s))
+    key = i.long() * m + j.long()
+    assert bool(torch.all(key[1:] > key[:-1]))
+    sizes = torch.from_numpy(sizes_np.astype(np.int32)).to(i.device)
+    assert bool(torch.all(sizes[i.long()] >= s)) and bool(torch.all(sizes[j.long()] >= s))
+    assert slg.last_stats()["wedges"] == oracle.wedges(m, n, off, idx, s)
