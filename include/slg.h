@@ -147,6 +147,24 @@ int slg_build_host(const slg_hypergraph *h, int32_t s, uint32_t flags,
 int slg_wedges(const slg_hypergraph *h, int32_t s, uint32_t flags,
                int64_t *wedges, void *stream);
 
+/*
+ * slg_tile_overlap -- exact overlap counts of a dense 0/1 block on the
+ * tensor cores: C = A·Aᵀ, the linear-algebra form of Section IV-D applied to
+ * a dense core of the incidence (the dense-core tile path).
+ *   A          device bytes [rows_pad x cols_pad], row-major, 0x38 (FP8 E4M3
+ *              1.0) for an incidence and 0x00 otherwise; 16-byte aligned
+ *   rows_pad   multiple of 128;  cols_pad  multiple of 128, < 2^24
+ *   C          device int32 [rows_pad x rows_pad], row-major; the tiles on
+ *              and above the diagonal (128 x 128 blocks bj >= bi) receive
+ *              C[i][j] = |row i ∩ row j| (exact: FP32 accumulation of 0/1
+ *              products stays integral below 2^24); the others are untouched
+ * Returns SLG_OK, SLG_ERR_INVALID (shape, alignment), SLG_ERR_UNSUPPORTED
+ * (no tensor-map support in the driver), SLG_ERR_TIMEOUT (a bounded
+ * device-side wait gave up), SLG_ERR_NOMEM, SLG_ERR_CUDA.
+ */
+int slg_tile_overlap(const uint8_t *A, int32_t rows_pad, int32_t cols_pad,
+                     int32_t *C, void *stream);
+
 /* Statistics of the last call made by this host thread.  Bins: 0 = warp
  * (small rows), 1 = CTA small, 2 = CTA large, 3 = giant rows. */
 typedef struct slg_stats {

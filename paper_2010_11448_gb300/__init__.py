@@ -20,7 +20,8 @@ import numpy as np
 
 __all__ = [
     "DeviceHypergraph", "to_device", "count", "build", "build_rows",
-    "build_host", "wedges", "last_stats", "set_profiling", "library_path", "load",
+    "build_host", "wedges", "last_stats", "set_profiling", "tile_overlap",
+    "library_path", "load",
     "SLG_DUAL", "SLG_UNWEIGHTED", "SLG_ALGO_BINNED", "SLG_ALGO_PLAIN",
     "SLG_ALGO_SPGEMM", "SlgError", "ABI_FUNCTIONS",
 ]
@@ -87,6 +88,7 @@ ABI_FUNCTIONS = {
     "slg_wedges": (ctypes.c_int, [_HP, ctypes.c_int32, ctypes.c_uint32, _I64P, _VP]),
     "slg_last_stats": (ctypes.c_int, [ctypes.POINTER(_Stats)]),
     "slg_set_profiling": (ctypes.c_int, [ctypes.c_int]),
+    "slg_tile_overlap": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP]),
     "slg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "slg_abi_version": (ctypes.c_int, []),
 }
@@ -285,6 +287,20 @@ def last_stats() -> dict:
             "kernel_launches": st.kernel_launches, "profiled": bool(st.profiled),
             "ms_plan": st.ms_plan, "ms_walk": list(st.ms_walk), "ms_scan": st.ms_scan,
             "ms_gather": st.ms_gather}
+
+
+def tile_overlap(A, stream=None):
+    """C = A·Aᵀ on the tensor cores for a dense 0/1 block.  ``A`` is a CUDA
+    uint8 tensor [rows_pad, cols_pad] (0x38 = 1, 0 = 0), both dimensions
+    multiples of 128; returns the int32 [rows_pad, rows_pad] tensor whose
+    tiles on and above the diagonal hold the overlap counts (others 0)."""
+    import torch
+    rows, cols = int(A.shape[0]), int(A.shape[1])
+    C = torch.zeros((rows, rows), dtype=torch.int32, device=A.device)
+    rc = load().slg_tile_overlap(A.data_ptr(), rows, cols, C.data_ptr(), _stream(stream))
+    if rc != 0:
+        raise SlgError(rc, "slg_tile_overlap")
+    return C
 
 
 def set_profiling(enable: bool) -> None:

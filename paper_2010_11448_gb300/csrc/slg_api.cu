@@ -100,7 +100,9 @@ int check_args(const slg_hypergraph *h, int32_t s, uint32_t flags) {
     return SLG_ERR_INVALID;
   if (!h->e_off || !h->v_off) return SLG_ERR_INVALID;
   if (h->nnz > 0 && (!h->e_idx || !h->v_idx)) return SLG_ERR_INVALID;
-  if ((flags & SLG_ALGO_MASK) != SLG_ALGO_BINNED) return SLG_ERR_UNSUPPORTED;
+  const uint32_t algo = flags & SLG_ALGO_MASK;
+  if (algo != SLG_ALGO_BINNED && algo != SLG_ALGO_PLAIN && algo != SLG_ALGO_SPGEMM)
+    return SLG_ERR_UNSUPPORTED;
   if (flags & ~(uint32_t)(SLG_DUAL | SLG_UNWEIGHTED | SLG_ALGO_MASK)) return SLG_ERR_INVALID;
   return SLG_OK;
 }
@@ -163,6 +165,286 @@ cudaError_t ensure_giant(DeviceCtx &c, size_t elems, cudaStream_t st) {
 
 enum Op { kOpCount, kOpBuild, kOpWedges };
 
+// Everything one call needs after argument checks.
+struct Call {
+  Side sd;
+  int32_t smin;
+  uint32_t flags;
+  bool unweighted;
+  int32_t row_begin, row_end, rows;
+  int32_t R_pad;
+  Op op;
+  int32_t *out_i, *out_j, *out_w;
+  int64_t capacity;
+  cudaStream_t st;
+  DeviceCtx *ctx;
+  Pool *pool;
+  Work w;
+  Events *evs;
+  int32_t launches;
+};
+
+int plain_warps() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms * 4;  // 4 warps per SM: a multiple of 8 (the kernel's block)
+}
+
+// Zero-initialised scratch of the plain kernel: per-warp dense counters
+// followed by the per-warp bitmaps (kept zero between calls).
+cudaError_t ensure_scratch(Call &c, size_t *summ_off) {
+  const size_t pw = (size_t)plain_warps();
+  const size_t rp = (size_t)c.R_pad;
+  const size_t counters = pw * rp;
+  *summ_off = counters;
+  return ensure_giant(*c.ctx, counters + pw * (rp >> 10), c.st);
+}
+
+// Per-CTA scratch of the giant bin: 3 ints per wedge of the largest row.
+cudaError_t giant_scratch(Call &c, int32_t max_work, WalkLaunch *L) {
+  L->giant_scratch = nullptr;
+  L->giant_stride = 0;
+  if (max_work <= 0) return cudaSuccess;
+  const long long stride = 3ll * max_work;
+  cudaError_t e = c.pool->get(&L->giant_scratch, (size_t)giant_ctas() * (size_t)stride);
+  if (e == cudaSuccess) L->giant_stride = stride;
+  return e;
+}
+
+int read_meta(Call &c) {
+  SLG_TRY(cudaMemcpyAsync(c.ctx->meta_host, c.w.meta, sizeof(Meta), cudaMemcpyDeviceToHost, c.st));
+  SLG_TRY(cudaStreamSynchronize(c.st));
+  return c.ctx->meta_host->err;
+}
+
+WalkLaunch walk_launch(Call &c, int mode, int32_t smin, int32_t list_base) {
+  WalkLaunch L = {};
+  L.a.mode = mode;
+  L.a.unweighted = c.unweighted;
+  L.a.smin = smin;
+  L.a.row_begin = list_base;
+  L.a.n_e = c.w.n_e;
+  L.a.stage_pos = c.w.stage_pos;
+  L.a.stage_j = c.w.stage_j;
+  L.a.stage_w = c.w.stage_w;
+  L.a.stage_cap = c.w.stage_cap;
+  L.a.meta = c.w.meta;
+  L.bin_rows = c.w.bin_rows;
+  L.row_work = c.w.row_work;
+  L.rows = c.rows;
+  L.R = c.sd.R;
+  return L;
+}
+
+// Default path: filtered CSC, binned single walk, staging, scan, gather.
+int run_binned(Call &c, int64_t *result) {
+  Work &w = c.w;
+  SLG_TRY(launch_filter(c.sd, c.smin, w, c.st));
+  SLG_TRY(launch_rows_work(c.sd, c.smin, c.row_begin, c.row_end, w, c.st));
+  c.launches += 4 + (c.rows > 0 ? 1 : 0);
+  if (c.op == kOpWedges) {
+    int rc = read_meta(c);
+    if (rc) return rc;
+    *result = (int64_t)c.ctx->meta_host->wedges;
+    return SLG_OK;
+  }
+  if (c.op == kOpBuild && c.capacity > 0) {
+    if (c.pool->get(&w.stage_j, (size_t)c.capacity) == cudaSuccess &&
+        (c.unweighted || c.pool->get(&w.stage_w, (size_t)c.capacity) == cudaSuccess))
+      w.stage_cap = c.capacity;
+    else
+      w.stage_cap = 0;  // rows that find no staging room are re-walked directly
+  }
+  // Planning totals: the giant bin's scratch is sized by its largest row.
+  int rc = read_meta(c);
+  if (rc) return rc;
+  const int32_t max_giant = c.ctx->meta_host->rows_bin[kBinGiant]
+                                ? c.ctx->meta_host->max_giant_work : 0;
+  WalkLaunch L = walk_launch(c, c.op == kOpBuild ? kStage : kCount, c.smin, c.row_begin);
+  SLG_TRY(giant_scratch(c, max_giant, &L));
+  L.w.r_off = c.sd.r_off;
+  L.w.r_idx = c.sd.r_idx;
+  L.w.c_off_s = w.c_off_s;
+  L.w.c_idx_s = w.c_idx_s;
+  L.w.tail_beg = w.tail_beg;
+  cudaEvent_t *ev = c.evs->on ? c.evs->ev + kEvWalk : nullptr;
+  if (c.rows > 0) {
+    SLG_TRY(launch_walk(L, c.st, &c.launches, ev));
+  } else if (ev) {
+    for (int b = 0; b <= kNumBins; ++b) cudaEventRecord(ev[b], c.st);
+  }
+  SLG_TRY(launch_row_scan(c.rows, w, c.st));
+  if (c.evs->on) cudaEventRecord(c.evs->ev[kEvScan], c.st);
+  c.launches += 3;
+  rc = read_meta(c);
+  if (rc) return rc;
+  const Meta &m = *c.ctx->meta_host;
+  const int64_t pairs = (int64_t)m.pairs;
+  *result = pairs;
+  if (c.op != kOpBuild) return SLG_OK;
+  if (pairs > c.capacity) return SLG_ERR_CAPACITY;
+  if (c.evs->on) cudaEventRecord(c.evs->ev[kEvGather0], c.st);
+  if (pairs > 0) {
+    if (m.stage_overflow == 0) {
+      SLG_TRY(launch_gather(c.row_begin, c.rows, w, c.out_i, c.out_j, c.out_w, c.unweighted,
+                            c.st));
+      c.launches += 1;
+    } else {
+      // Staging too small: walk again, writing straight to the output.
+      SLG_TRY(cudaMemsetAsync(&w.meta->giant_ticket, 0, sizeof(unsigned int), c.st));
+      L.a.mode = kDirect;
+      L.a.row_ptr = w.row_ptr;
+      L.a.out_i = c.out_i;
+      L.a.out_j = c.out_j;
+      L.a.out_w = c.out_w;
+      SLG_TRY(launch_walk(L, c.st, &c.launches));
+    }
+  }
+  if (c.evs->on) cudaEventRecord(c.evs->ev[kEvGather1], c.st);
+  rc = read_meta(c);
+  return rc;
+}
+
+// Plain comparison path: count pass, scan, write pass (two walks).
+int run_plain(Call &c, int64_t *result) {
+  Work &w = c.w;
+  size_t summ_off = 0;
+  SLG_TRY(ensure_scratch(c, &summ_off));
+  const int32_t pw = plain_warps();
+  EmitArgs a = {};
+  a.mode = kCount;
+  a.unweighted = c.unweighted;
+  a.smin = c.smin;
+  a.row_begin = c.row_begin;
+  a.n_e = w.n_e;
+  a.meta = w.meta;
+  uint32_t *summ = reinterpret_cast<uint32_t *>(c.ctx->giant + summ_off);
+  if (c.evs->on) cudaEventRecord(c.evs->ev[kEvWalk], c.st);
+  if (c.rows > 0)
+    SLG_TRY(launch_plain(c.sd, c.smin, c.row_begin, c.row_end, a, c.ctx->giant, summ, c.R_pad,
+                         pw, c.st));
+  if (c.evs->on)
+    for (int b = 1; b <= kNumBins; ++b) cudaEventRecord(c.evs->ev[kEvWalk + b], c.st);
+  SLG_TRY(launch_row_scan(c.rows, w, c.st));
+  if (c.evs->on) cudaEventRecord(c.evs->ev[kEvScan], c.st);
+  c.launches += 4;
+  int rc = read_meta(c);
+  if (rc) return rc;
+  const int64_t pairs = (int64_t)c.ctx->meta_host->pairs;
+  *result = c.op == kOpWedges ? (int64_t)c.ctx->meta_host->wedges : pairs;
+  if (c.op != kOpBuild) return SLG_OK;
+  if (pairs > c.capacity) return SLG_ERR_CAPACITY;
+  if (c.evs->on) cudaEventRecord(c.evs->ev[kEvGather0], c.st);
+  if (pairs > 0 && c.rows > 0) {
+    a.mode = kDirect;
+    a.row_ptr = w.row_ptr;
+    a.out_i = c.out_i;
+    a.out_j = c.out_j;
+    a.out_w = c.out_w;
+    SLG_TRY(launch_plain(c.sd, c.smin, c.row_begin, c.row_end, a, c.ctx->giant, summ, c.R_pad,
+                         pw, c.st));
+    c.launches += 1;
+  }
+  if (c.evs->on) cudaEventRecord(c.evs->ev[kEvGather1], c.st);
+  return read_meta(c);
+}
+
+// Filtered SpGEMM comparison path: product rows (full columns, both
+// triangles, threshold 1) materialised chunk by chunk, then filtered.
+int run_spgemm(Call &c, int64_t *result) {
+  Work &w = c.w;
+  const int32_t rows = c.rows;
+  int32_t *work = nullptr, *kept = nullptr;
+  long long *prefix = nullptr, *chunk_ptr = nullptr;
+  SLG_TRY(c.pool->get(&work, (size_t)rows + 1));
+  SLG_TRY(c.pool->get(&kept, (size_t)rows + 1));
+  SLG_TRY(c.pool->get(&prefix, (size_t)rows + 1));
+  SLG_TRY(c.pool->get(&chunk_ptr, (size_t)rows + 1));
+  // 1. product-row sizes (upper bounds: sum of column lengths) and prefix
+  SLG_TRY(launch_rows_full(c.sd, c.row_begin, c.row_end, c.row_begin, w.tail_beg, work, w.n_e,
+                           w.stage_pos, nullptr, rows, w.meta, c.st));
+  Work wp = w;
+  wp.n_e = work;
+  wp.row_ptr = prefix;
+  SLG_TRY(launch_row_scan(rows, wp, c.st));
+  c.launches += 4;
+  std::vector<long long> pre((size_t)rows + 1);
+  SLG_TRY(cudaMemcpyAsync(pre.data(), prefix, sizeof(long long) * (rows + 1),
+                          cudaMemcpyDeviceToHost, c.st));
+  int rc = read_meta(c);
+  if (rc) return rc;
+  const long long total_work = pre[rows];
+  if (c.op == kOpWedges) {
+    *result = total_work;
+    return SLG_OK;
+  }
+  // 2. staging budget for one chunk of product rows
+  long long budget = total_work < (1ll << 30) ? total_work : (1ll << 30);
+  long long max_row = 0;
+  for (int32_t r = 0; r < rows; ++r)
+    if (pre[r + 1] - pre[r] > max_row) max_row = pre[r + 1] - pre[r];
+  if (budget < max_row) budget = max_row;
+  if (budget < 1) budget = 1;
+  SLG_TRY(c.pool->get(&w.stage_j, (size_t)budget));
+  SLG_TRY(c.pool->get(&w.stage_w, (size_t)budget));
+  w.stage_cap = budget;
+  WalkLaunch Lg = walk_launch(c, kStage, 1, c.row_begin);
+  Lg.a.full_rows = 1;
+  SLG_TRY(giant_scratch(c, max_row > kCtaLMaxWork ? (int32_t)max_row : 0, &Lg));
+  long long total_out = 0, products = 0;
+  int32_t r0 = 0;
+  if (c.evs->on) cudaEventRecord(c.evs->ev[kEvWalk], c.st);
+  while (r0 < rows) {
+    int32_t r1 = r0 + 1;
+    while (r1 < rows && pre[r1 + 1] - pre[r0] <= budget) ++r1;
+    const int32_t a0 = c.row_begin + r0, a1 = c.row_begin + r1;
+    SLG_TRY(cudaMemsetAsync(w.meta, 0, sizeof(Meta), c.st));
+    SLG_TRY(launch_rows_full(c.sd, a0, a1, c.row_begin, w.tail_beg, w.row_work, w.n_e,
+                             w.stage_pos, w.bin_rows, rows, w.meta, c.st));
+    WalkLaunch L = Lg;
+    L.w.r_off = c.sd.r_off;
+    L.w.r_idx = c.sd.r_idx;
+    L.w.c_off_s = c.sd.c_off;
+    L.w.c_idx_s = c.sd.c_idx;
+    L.w.tail_beg = w.tail_beg;
+    SLG_TRY(launch_walk(L, c.st, &c.launches));
+    SLG_TRY(launch_filter_count(a0, a1, c.row_begin, w, c.smin, kept, c.st));
+    Work wf = w;
+    wf.n_e = kept;
+    wf.row_ptr = chunk_ptr;
+    SLG_TRY(launch_row_scan(r1 - r0, wf, c.st));
+    c.launches += 5;
+    rc = read_meta(c);
+    if (rc) return rc;
+    const Meta &m = *c.ctx->meta_host;
+    if (m.stage_overflow) return SLG_ERR_NOMEM;  // cannot happen: chunk fits the budget
+    const long long got = (long long)m.pairs;
+    products += (long long)m.stage_cursor;
+    if (c.op == kOpBuild && total_out + got <= c.capacity && got > 0) {
+      SLG_TRY(launch_filter_write(a0, a1, c.row_begin, w, c.smin, chunk_ptr, total_out,
+                                  c.unweighted, c.out_i, c.out_j, c.out_w, c.st));
+      c.launches += 1;
+    }
+    total_out += got;
+    r0 = r1;
+  }
+  if (c.evs->on) {
+    for (int b = 1; b <= kNumBins; ++b) cudaEventRecord(c.evs->ev[kEvWalk + b], c.st);
+    cudaEventRecord(c.evs->ev[kEvScan], c.st);
+    cudaEventRecord(c.evs->ev[kEvGather0], c.st);
+    cudaEventRecord(c.evs->ev[kEvGather1], c.st);
+  }
+  rc = read_meta(c);
+  if (rc) return rc;
+  c.ctx->meta_host->pairs = (unsigned long long)total_out;
+  c.ctx->meta_host->wedges = (unsigned long long)total_work;
+  c.ctx->meta_host->stage_cursor = (unsigned long long)products;
+  *result = total_out;
+  if (c.op == kOpBuild && total_out > c.capacity) return SLG_ERR_CAPACITY;
+  return SLG_OK;
+}
+
 // The whole pipeline for one side, one s and one row range.
 int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin,
         int32_t row_end, Op op, int32_t *out_i, int32_t *out_j, int32_t *out_w,
@@ -170,137 +452,77 @@ int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin
   int rc = check_args(h, smin, flags);
   if (rc != SLG_OK) return rc;
   if (!result) return SLG_ERR_INVALID;
-  const Side sd = side_of(h, flags);
-  if (row_begin < 0 || row_end < row_begin || row_end > sd.R) return SLG_ERR_INVALID;
-  const bool unweighted = (flags & SLG_UNWEIGHTED) != 0;
+  Call c = {};
+  c.sd = side_of(h, flags);
+  if (row_begin < 0 || row_end < row_begin || row_end > c.sd.R) return SLG_ERR_INVALID;
+  c.smin = smin;
+  c.flags = flags;
+  c.unweighted = (flags & SLG_UNWEIGHTED) != 0;
   if (op == kOpBuild) {
     if (capacity < 0) return SLG_ERR_INVALID;
-    if (capacity > 0 && (!out_i || !out_j || (!unweighted && !out_w))) return SLG_ERR_INVALID;
+    if (capacity > 0 && (!out_i || !out_j || (!c.unweighted && !out_w))) return SLG_ERR_INVALID;
   }
-  const int32_t rows = row_end - row_begin;
-  const int64_t nnz = sd.nnz;
-  const int32_t R_pad = (int32_t)(((int64_t)sd.R + 1023) / 1024 * 1024);
-  if (giant_smem_bytes(R_pad > 0 ? R_pad : 1024) > 200 * 1024) return SLG_ERR_UNSUPPORTED;
+  c.row_begin = row_begin;
+  c.row_end = row_end;
+  c.rows = row_end - row_begin;
+  c.op = op;
+  c.out_i = out_i;
+  c.out_j = out_j;
+  c.out_w = out_w;
+  c.capacity = capacity;
+  c.st = st;
+  const int64_t nnz = c.sd.nnz;
+  c.R_pad = (int32_t)(((int64_t)c.sd.R + 1023) / 1024 * 1024);
+  if (c.R_pad == 0) c.R_pad = 1024;
+  if (c.sd.R > kGiantMaxR) return SLG_ERR_UNSUPPORTED;
 
   int dev = 0;
-  DeviceCtx &c = ctx_for_current(&dev);
-  std::lock_guard<std::mutex> lock(c.mu);
-  ensure_pool(c, dev);
-  if (!c.meta_host) SLG_TRY(cudaMallocHost(&c.meta_host, sizeof(Meta)));
+  DeviceCtx &ctx = ctx_for_current(&dev);
+  std::lock_guard<std::mutex> lock(ctx.mu);
+  ensure_pool(ctx, dev);
+  if (!ctx.meta_host) SLG_TRY(cudaMallocHost(&ctx.meta_host, sizeof(Meta)));
+  c.ctx = &ctx;
 
-  slg_stats stats = {};
-  int32_t launches = 0;
   Events evs(t_profile != 0 && op != kOpWedges);
   Pool pool(st);
-  Work w = {};
+  c.pool = &pool;
+  c.evs = &evs;
+  Work &w = c.w;
   const int32_t ntiles = (int32_t)((nnz + 4095) / 4096);
-  const int32_t ntiles64 = (rows + 4095) / 4096;
+  const int32_t ntiles64 = (c.rows + 4095) / 4096;
   SLG_TRY(pool.get(&w.meta, 1));
   SLG_TRY(pool.get(&w.csr2csc, (size_t)nnz));
   SLG_TRY(pool.get(&w.qs, (size_t)nnz + 1));
   SLG_TRY(pool.get(&w.c_idx_s, (size_t)nnz));
-  SLG_TRY(pool.get(&w.c_off_s, (size_t)sd.C + 1));
+  SLG_TRY(pool.get(&w.c_off_s, (size_t)c.sd.C + 1));
   SLG_TRY(pool.get(&w.tail_beg, (size_t)nnz));
   SLG_TRY(pool.get(&w.tile, (size_t)ntiles + 1));
-  SLG_TRY(pool.get(&w.bin_rows, (size_t)kNumBins * (rows > 0 ? rows : 1)));
-  SLG_TRY(pool.get(&w.n_e, (size_t)rows + 1));
-  SLG_TRY(pool.get(&w.stage_pos, (size_t)rows + 1));
-  SLG_TRY(pool.get(&w.row_ptr, (size_t)rows + 1));
+  SLG_TRY(pool.get(&w.bin_rows, (size_t)kNumBins * (c.rows > 0 ? c.rows : 1)));
+  SLG_TRY(pool.get(&w.n_e, (size_t)c.rows + 1));
+  SLG_TRY(pool.get(&w.row_work, (size_t)c.rows + 1));
+  SLG_TRY(pool.get(&w.stage_pos, (size_t)c.rows + 1));
+  SLG_TRY(pool.get(&w.row_ptr, (size_t)c.rows + 1));
   SLG_TRY(pool.get(&w.tile64, (size_t)ntiles64 + 1));
   SLG_TRY(cudaMemsetAsync(w.meta, 0, sizeof(Meta), st));
 
-  // Planning: validation, CSR->CSC map, filtered CSC, tails, work, bins.
+  // Validation and the CSR->CSC map (a consistency check for every path).
   if (evs.on) cudaEventRecord(evs.ev[kEvPlan], st);
-  SLG_TRY(launch_validate(sd, w.meta, st));
-  SLG_TRY(launch_csr2csc(sd, w.csr2csc, w.meta, st));
-  SLG_TRY(launch_filter(sd, smin, w, st));
-  SLG_TRY(launch_rows_work(sd, smin, row_begin, row_end, w, st));
-  launches += 2 + 1 + 4 + (rows > 0 ? 1 : 0);
+  SLG_TRY(launch_validate(c.sd, w.meta, st));
+  SLG_TRY(launch_csr2csc(c.sd, w.csr2csc, w.meta, st));
+  c.launches += 3;
 
-  int64_t pairs = 0;
-  if (op != kOpWedges) {
-    // Staging for the single-walk build: sized by the caller's capacity; if
-    // it cannot be had the rows that do not fit are re-walked directly.
-    if (op == kOpBuild && capacity > 0) {
-      if (pool.get(&w.stage_j, (size_t)capacity) == cudaSuccess &&
-          (unweighted || pool.get(&w.stage_w, (size_t)capacity) == cudaSuccess)) {
-        w.stage_cap = capacity;
-      } else {
-        w.stage_cap = 0;
-      }
-    }
-    const int32_t gctas = giant_ctas_for_device();
-    SLG_TRY(ensure_giant(c, (size_t)gctas * (size_t)R_pad, st));
-    WalkLaunch L = {};
-    L.w.r_off = sd.r_off;
-    L.w.r_idx = sd.r_idx;
-    L.w.c_off_s = w.c_off_s;
-    L.w.c_idx_s = w.c_idx_s;
-    L.w.tail_beg = w.tail_beg;
-    L.a.mode = (op == kOpBuild) ? kStage : kCount;
-    L.a.unweighted = unweighted;
-    L.a.smin = smin;
-    L.a.row_begin = row_begin;
-    L.a.n_e = w.n_e;
-    L.a.stage_pos = w.stage_pos;
-    L.a.stage_j = w.stage_j;
-    L.a.stage_w = w.stage_w;
-    L.a.stage_cap = w.stage_cap;
-    L.a.meta = w.meta;
-    L.bin_rows = w.bin_rows;
-    L.rows = rows;
-    L.giant_scratch = c.giant;
-    L.giant_ctas = gctas;
-    L.R_pad = R_pad;
-    if (rows > 0) {
-      SLG_TRY(launch_walk(L, st, &launches, evs.on ? evs.ev + kEvWalk : nullptr));
-    } else if (evs.on) {
-      for (int b = 0; b <= kNumBins; ++b) cudaEventRecord(evs.ev[kEvWalk + b], st);
-    }
-    SLG_TRY(launch_row_scan(rows, w, st));
-    if (evs.on) cudaEventRecord(evs.ev[kEvScan], st);
-    launches += 1 + 2 * (ntiles64 > 0);
-    SLG_TRY(cudaMemcpyAsync(c.meta_host, w.meta, sizeof(Meta), cudaMemcpyDeviceToHost, st));
-    SLG_TRY(cudaStreamSynchronize(st));
-    const Meta &m = *c.meta_host;
-    if (m.err) return m.err;
-    pairs = (int64_t)m.pairs;
-    if (op == kOpBuild) {
-      if (pairs > capacity) {
-        *result = pairs;
-        return SLG_ERR_CAPACITY;
-      }
-      if (evs.on) cudaEventRecord(evs.ev[kEvGather0], st);
-      if (pairs > 0) {
-        if (m.stage_overflow == 0) {
-          SLG_TRY(launch_gather(row_begin, rows, w, out_i, out_j, out_w, unweighted, st));
-          launches += 1;
-        } else {
-          // Staging too small: walk again, writing straight to the output.
-          SLG_TRY(cudaMemsetAsync(&w.meta->giant_ticket, 0, sizeof(unsigned int), st));
-          L.a.mode = kDirect;
-          L.a.row_ptr = w.row_ptr;
-          L.a.out_i = out_i;
-          L.a.out_j = out_j;
-          L.a.out_w = out_w;
-          SLG_TRY(launch_walk(L, st, &launches));
-        }
-        SLG_TRY(cudaMemcpyAsync(c.meta_host, w.meta, sizeof(Meta), cudaMemcpyDeviceToHost, st));
-      }
-      if (evs.on) cudaEventRecord(evs.ev[kEvGather1], st);
-      SLG_TRY(cudaStreamSynchronize(st));
-      if (c.meta_host->err) return c.meta_host->err;
-    }
-    *result = pairs;
-  } else {
-    SLG_TRY(cudaMemcpyAsync(c.meta_host, w.meta, sizeof(Meta), cudaMemcpyDeviceToHost, st));
-    SLG_TRY(cudaStreamSynchronize(st));
-    if (c.meta_host->err) return c.meta_host->err;
-    *result = (int64_t)c.meta_host->wedges;
-  }
-  const Meta &m = *c.meta_host;
+  int64_t value = 0;
+  const uint32_t algo = flags & SLG_ALGO_MASK;
+  if (algo == SLG_ALGO_PLAIN) rc = run_plain(c, &value);
+  else if (algo == SLG_ALGO_SPGEMM) rc = run_spgemm(c, &value);
+  else rc = run_binned(c, &value);
+  if (rc == SLG_OK || rc == SLG_ERR_CAPACITY) *result = value;
+  if (rc != SLG_OK) return rc;
+
+  slg_stats stats = {};
+  const Meta &m = *ctx.meta_host;
   stats.wedges = (int64_t)m.wedges;
-  stats.pairs = pairs;
+  stats.pairs = op == kOpWedges ? 0 : value;
   stats.rows_active = (int64_t)m.active;
   for (int b = 0; b < kNumBins; ++b) {
     stats.rows_bin[b] = (int64_t)m.rows_bin[b];
@@ -308,7 +530,7 @@ int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin
     stats.incid_bin[b] = (int64_t)m.incid_bin[b];
     stats.pairs_bin[b] = (int64_t)m.pairs_bin[b];
   }
-  stats.kernel_launches = launches;
+  stats.kernel_launches = c.launches;
   if (evs.on) {
     stats.profiled = 1;
     stats.ms_plan = evs.ms(kEvPlan, kEvWalk);
@@ -403,6 +625,29 @@ int slg_build_host(const slg_hypergraph *hh, int32_t s, uint32_t flags, int32_t 
   }
   SLG_TRY(cudaStreamSynchronize(st));
   return SLG_OK;
+}
+
+int slg_tile_overlap(const uint8_t *A, int32_t rows_pad, int32_t cols_pad, int32_t *C,
+                     void *stream) {
+  if (!A || !C || rows_pad <= 0 || cols_pad <= 0 || rows_pad % 128 || cols_pad % 128 ||
+      cols_pad >= (1 << 24) || (reinterpret_cast<uintptr_t>(A) & 15))
+    return SLG_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  Pool pool(st);
+  const int64_t nt = rows_pad / 128;
+  void *tasks = nullptr;
+  int32_t *err = nullptr;
+  SLG_TRY(pool.get(reinterpret_cast<int64_t **>(&tasks), (size_t)(nt * (nt + 1) / 2)));
+  SLG_TRY(pool.get(&err, 1));
+  SLG_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
+  cudaError_t e = launch_tile_overlap(A, rows_pad, cols_pad, C, tasks, err, st);
+  if (e == cudaErrorNotSupported) return SLG_ERR_UNSUPPORTED;
+  if (e == cudaErrorInvalidValue) return SLG_ERR_INVALID;
+  SLG_TRY(e);
+  int32_t h_err = 0;
+  SLG_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  SLG_TRY(cudaStreamSynchronize(st));
+  return h_err ? SLG_ERR_TIMEOUT : SLG_OK;
 }
 
 int slg_set_profiling(int enable) {

@@ -44,6 +44,7 @@ struct Meta {
   unsigned long long stage_overflow;   // rows that did not fit the staging
   unsigned int giant_ticket;           // dynamic giant-row scheduling
   int32_t kept;                        // entries of the filtered CSC
+  int32_t max_giant_work;              // largest work of a giant-bin row
 };
 
 // Where a device-side check fired (for error reports).
@@ -247,6 +248,7 @@ struct Work {
   int32_t *tile;       // [ntiles + 1] scan scratch
   int32_t *bin_rows;   // [kNumBins][R] row lists
   int32_t *n_e;        // [R] pairs per row
+  int32_t *row_work;   // [R] wedges per row
   long long *stage_pos;// [R] staging offset per row, -1 = not staged
   long long *row_ptr;  // [R + 1] output offsets (relative to row_begin)
   long long *tile64;   // [ntiles64 + 1]
@@ -268,6 +270,7 @@ enum Mode : int { kCount = 0, kStage = 1, kDirect = 2 };
 struct EmitArgs {
   int mode;
   int unweighted;
+  int full_rows;                      // 1: tails are whole columns, far ends in [0, R)
   int32_t smin;
   int32_t row_begin;
   int32_t *n_e;                       // [rows] pairs per row
@@ -283,11 +286,16 @@ struct WalkLaunch {
   Walk w;
   EmitArgs a;
   const int32_t *bin_rows;  // [kNumBins][rows] row lists
+  const int32_t *row_work;  // [rows] wedges per row
   int32_t rows;             // rows in the range (list stride)
-  int32_t *giant_scratch;   // [giant_ctas][R_pad] zero-initialised counters
-  int32_t giant_ctas;
-  int32_t R_pad;            // R rounded up to a multiple of 1024
+  int32_t *giant_scratch;   // [giant_ctas][3 * max giant work] wedge ends + pairs
+  long long giant_stride;   // ints per giant CTA
+  int32_t R;                // rows of the side (far ends lie in [0, R))
 };
+
+// CTAs of the giant kernel (one per SM) and the largest side it supports.
+int giant_ctas();
+constexpr int32_t kGiantMaxR = 1 << 24;
 
 // ev (optional): kNumBins + 1 events recorded before the first and after
 // every bin kernel.
@@ -298,6 +306,30 @@ cudaError_t launch_gather(int32_t row_begin, int32_t rows, const Work &w, int32_
                           int32_t *out_j, int32_t *out_w, int unweighted, cudaStream_t st);
 
 int giant_ctas_for_device();
-size_t giant_smem_bytes(int32_t R);
+
+// Plain per-hyperedge kernel (comparison): `warps` warps, each with R_pad
+// counters in `scratch` and R_pad/1024 bitmap words in `summ`, all zero.
+cudaError_t launch_plain(const Side &sd, int32_t smin, int32_t row_begin, int32_t row_end,
+                         const EmitArgs &a, int32_t *scratch, uint32_t *summ, int32_t R_pad,
+                         int32_t warps, cudaStream_t st);
+
+// Dense-core tile path (tcgen05): C = A·Aᵀ on the upper-triangle 128 x 128
+// tiles of an Mp x Kp byte matrix A (0x38 = 1.0).  `tasks` holds room for
+// nt (nt + 1) / 2 tile pairs (nt = Mp / 128), `err` one device int.
+cudaError_t launch_tile_overlap(const uint8_t *A, int32_t Mp, int32_t Kp, int32_t *C,
+                                void *tasks, int32_t *err, cudaStream_t st);
+size_t tile_overlap_smem();
+
+// Filtered SpGEMM comparison: full-column tails / per-row work, filtration.
+cudaError_t launch_rows_full(const Side &sd, int32_t row_begin, int32_t row_end,
+                             int32_t list_base, int32_t *tail_beg, int32_t *work_out,
+                             int32_t *n_e, long long *stage_pos, int32_t *bin_rows,
+                             int32_t list_stride, Meta *meta, cudaStream_t st);
+cudaError_t launch_filter_count(int32_t row_begin, int32_t row_end, int32_t list_base,
+                                const Work &w, int32_t smin, int32_t *kept, cudaStream_t st);
+cudaError_t launch_filter_write(int32_t row_begin, int32_t row_end, int32_t list_base,
+                                const Work &w, int32_t smin, const long long *row_ptr,
+                                long long out_base, int unweighted, int32_t *out_i,
+                                int32_t *out_j, int32_t *out_w, cudaStream_t st);
 
 }  // namespace slg

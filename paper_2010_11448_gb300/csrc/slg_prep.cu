@@ -183,6 +183,7 @@ __global__ __launch_bounds__(kRowsNT) void k_rows_work(Side s, int32_t smin, int
                                                        int32_t *__restrict__ tail_beg,
                                                        int32_t *__restrict__ n_e,
                                                        long long *__restrict__ stage_pos,
+                                                       int32_t *__restrict__ row_work,
                                                        int32_t *__restrict__ bin_rows,
                                                        Meta *meta) {
   if (meta->err) return;
@@ -214,6 +215,7 @@ __global__ __launch_bounds__(kRowsNT) void k_rows_work(Side s, int32_t smin, int
       if (lane == 0) {
         n_e[e - row_begin] = 0;
         stage_pos[e - row_begin] = -1;
+        row_work[e - row_begin] = work;
       }
     }
     if (lane == 0) s_work[i] = (e < row_end) ? work : 0;
@@ -225,6 +227,7 @@ __global__ __launch_bounds__(kRowsNT) void k_rows_work(Side s, int32_t smin, int
     my_work = s_work[threadIdx.x];
     if (my_work > 0) {
       my_bin = bin_of(my_work);
+      if (my_bin == kBinGiant) atomicMax(&meta->max_giant_work, my_work);
       my_slot = atomicAdd(&s_cnt[my_bin], 1);
       atomicAdd(&s_w[my_bin], (unsigned long long)my_work);
       const int32_t e = r0 + threadIdx.x;
@@ -297,7 +300,8 @@ cudaError_t launch_rows_work(const Side &s, int32_t smin, int32_t row_begin, int
   if (rows <= 0) return cudaSuccess;
   const int grid = (rows + kRowsPerBlock - 1) / kRowsPerBlock;
   k_rows_work<<<grid, kRowsNT, 0, st>>>(s, smin, row_begin, row_end, w.csr2csc, w.qs, w.c_off_s,
-                                        w.tail_beg, w.n_e, w.stage_pos, w.bin_rows, w.meta);
+                                        w.tail_beg, w.n_e, w.stage_pos, w.row_work, w.bin_rows,
+                                        w.meta);
   return cudaGetLastError();
 }
 
