@@ -53,6 +53,18 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (testing)")
+    ap.add_argument("--builds", default="all",
+                    help="comma list of builds to run, e.g. 'H:8,H*:2' (profiling)")
+    ap.add_argument("--mode", choices=["headline", "batch", "serve", "core"], default="headline",
+                    help="headline: the Chung-Lu build (default); batch: many hypergraphs "
+                         "in one captured pipeline vs sequential builds; serve: Poisson "
+                         "query stream; core: planted dense core with and without the "
+                         "tensor-core tile path")
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--batch-max", type=int, default=200_000)
+    ap.add_argument("--queries", type=int, default=2000)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--core-scale", type=float, default=1.0)
     return ap.parse_args()
 
 
@@ -87,8 +99,14 @@ def make_workload(rank: int, scale: float):
     return hypergen.chung_lu(name=WORKLOAD, **c)
 
 
+_ONLY = None
+
+
 def jobs():
-    return [(dual, s) for dual in SIDES for s in S_VALUES]
+    all_jobs = [(dual, s) for dual in SIDES for s in S_VALUES]
+    if _ONLY is None:
+        return all_jobs
+    return [j for j in all_jobs if j in _ONLY]
 
 
 # ------------------------------------------------------------------ clocks --
@@ -165,13 +183,13 @@ def peaks():
 def walk_bytes(st, b):
     """Algorithmic bytes of the bin-b walk kernel in one build: per row its
     list entry, CSR offsets, count and staging offset (24 B); per incidence
-    its column id, tail start and the column's end offset (12 B); per wedge
-    the far end's id (4 B); per pair its staged (j, w) (8 B)."""
-    return (24 * st["rows_bin"][b] + 12 * st["incid_bin"][b] + 4 * st["wedges_bin"][b]
+    its tail bounds (8 B); per wedge the far end's id (4 B); per pair its
+    staged (j, w) (8 B)."""
+    return (24 * st["rows_bin"][b] + 8 * st["incid_bin"][b] + 4 * st["wedges_bin"][b]
             + 8 * st["pairs_bin"][b])
 
 
-WALK_KERNELS = ["k_walk_warp", "k_walk_cta<256,2048>", "k_walk_cta<1024,16384>",
+WALK_KERNELS = ["k_walk_warp", "k_walk_cta<256,2048>", "k_walk_cta<256,8192>",
                 "k_walk_giant"]
 
 
@@ -410,10 +428,190 @@ def run_ours(args):
     return 0
 
 
+# --------------------------------------------------------------- other modes --
+
+def _setup_gpu():
+    import torch
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    import paper_2010_11448_gb300 as slg
+    from paper_2010_11448_gb300 import build_lib
+    build_lib.build()
+    slg.load()
+    return torch, slg
+
+
+def run_batch(args):
+    """Batched form: `batch_count` Chung-Lu hypergraphs (m log-uniform in
+    [1e3, batch_max], n = 2m), each with its own s ~ U{2..32}: one captured
+    pipeline (graph replay) vs the same builds one call at a time (binned, and
+    the plain per-hyperedge kernel)."""
+    import numpy as np
+    torch, slg = _setup_gpu()
+    import hypergen
+    t0 = time.perf_counter()
+    members = hypergen.batch(args.batch_count, seed=100, m_lo=1000, m_hi=args.batch_max)
+    gen_s = time.perf_counter() - t0
+    dhs = [slg.to_device(h) for h, _ in members]
+    ss = [s for _, s in members]
+    W = sum(slg.wedges(d, s) for d, s in zip(dhs, ss))
+    t0 = time.perf_counter()
+    plan = slg.Plan(dhs, ss)
+    plan_s = time.perf_counter() - t0
+    info = plan.info()
+    st = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        plan.execute()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        plan.execute()
+    e1.record(st)
+    torch.cuda.synchronize()
+    batched_ms = e0.elapsed_time(e1) / args.steps
+    res = plan.results()
+    pairs = sum(int(r[0].shape[0]) for r in res)
+    # sequential builds, binned and plain (each call sizes its own output)
+    caps = [slg.count(d, s) for d, s in zip(dhs, ss)]
+    outs = [slg.alloc_outputs(c) for c in caps]
+    seq = {}
+    for algo in ("binned", "plain"):
+        for d, s, o in zip(dhs, ss, outs):        # warm
+            slg.build(d, s, algo=algo, out=o)
+            break
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for d, s, o in zip(dhs, ss, outs):
+            slg.build(d, s, algo=algo, out=o)
+        torch.cuda.synchronize()
+        seq[algo] = (time.perf_counter() - t) * 1e3
+    # the batched result equals the sequential one, member by member
+    same = all(torch.equal(r[1], o[1][:c]) and torch.equal(r[2], o[2][:c])
+               for r, o, c in zip(res, outs, caps))
+    out = {"mode": "batch", "metric": "batched L_s build: one captured launch vs sequential",
+           "members": len(dhs), "incidences": int(sum(d.nnz for d in dhs)),
+           "wedges": int(W), "pairs": pairs, "batched_ms": batched_ms,
+           "batched_wedges_per_s": W / (batched_ms / 1e3),
+           "sequential_binned_ms": seq["binned"], "sequential_plain_ms": seq["plain"],
+           "speedup_vs_plain": seq["plain"] / batched_ms,
+           "speedup_vs_sequential_binned": seq["binned"] / batched_ms,
+           "bit_identical_to_sequential": bool(same), "autotuned_bins": info["bins"],
+           "kernels_per_launch": info["launches"], "plan_s": plan_s, "generate_s": gen_s,
+           "steps": args.steps, "warmup": args.warmup}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Serving form: a resident pool of 16 Chung-Lu hypergraphs (the headline
+    recipe scaled 0.05x-1x, geometric), a Poisson stream of queries (graph
+    U{0..15}, s U{1..64}, side Bernoulli(0.5)) at `rate` per second."""
+    import numpy as np
+    torch, slg = _setup_gpu()
+    import hypergen
+    from paper_2010_11448_gb300.serve import Server
+    scales = np.geomspace(0.05, 1.0, 16)
+    c = dict(hypergen.CONFIGS[WORKLOAD])
+    graphs = [hypergen.chung_lu(int(c["m"] * sc), int(c["n"] * sc), seed=200 + k)
+              for k, sc in enumerate(scales)]
+    dhs = [slg.to_device(h) for h in graphs]
+    rng = np.random.default_rng(5)
+    n = args.queries
+    gaps = rng.exponential(1.0 / args.rate, size=n)
+    qs_spec = [(int(rng.integers(0, 16)), int(rng.integers(1, 65)), bool(rng.integers(0, 2)))
+               for _ in range(n)]
+    srv = Server(dhs, slots=4, memory_budget=96 << 30)
+    t0 = time.perf_counter()
+    due = t0
+    queries = []
+    for gap, spec in zip(gaps, qs_spec):
+        due += gap
+        now = time.perf_counter()
+        if due > now:
+            time.sleep(due - now)
+        queries.append(srv.submit(*spec))
+    for q in queries:
+        q.wait()
+    wall = time.perf_counter() - t0
+    srv.close()
+    summ = Server.summary(queries, wall)
+    # the same queries one at a time through the plain kernel (first 100)
+    k = min(100, n)
+    lat = []
+    for gid, s, dual in qs_spec[:k]:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        slg.build(dhs[gid], s, dual=dual, algo="plain")
+        torch.cuda.synchronize()
+        lat.append((time.perf_counter() - t) * 1e3)
+    lat = np.array(lat)
+    out = {"mode": "serve", "metric": "s-line-graph queries: latency and throughput",
+           "rate_per_s": args.rate, "slots": 4, **summ,
+           "plain_one_at_a_time": {"queries": k, "p50_ms": float(np.percentile(lat, 50)),
+                                   "p99_ms": float(np.percentile(lat, 99)),
+                                   "queries_per_s": k / (lat.sum() / 1e3)}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_core(args):
+    """Dense core: the lognormal web-shaped hypergraph with a planted core of
+    4096 hyperedges x 8192 vertices at density 0.3; builds at s = 2, 8, 32 on
+    H and H*, with and without the tensor-core tile path (same output)."""
+    torch, slg = _setup_gpu()
+    import hypergen
+    sc = args.core_scale
+    t0 = time.perf_counter()
+    h = hypergen.lognormal_web(int(4_000_000 * sc), int(10_000_000 * sc), seed=2)
+    gen_s = time.perf_counter() - t0
+    dh = slg.to_device(h)
+    rows = {}
+    for dual in (False, True):
+        for s in (2, 8, 32):
+            n = slg.count(dh, s, dual, tensor=True)
+            o = slg.alloc_outputs(n)
+            res = {}
+            for tensor in (True, False):
+                slg.build(dh, s, dual=dual, out=o, tensor=tensor)   # warm
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                i, j, w = slg.build(dh, s, dual=dual, out=o, tensor=tensor)
+                torch.cuda.synchronize()
+                ms = (time.perf_counter() - t) * 1e3
+                st = slg.last_stats()
+                res["tile" if tensor else "walk"] = {"ms": ms, "wedges_walked": st["wedges"],
+                                                     "core": [st["core_rows"], st["core_cols"]]}
+                if tensor:
+                    ref = (i.clone(), j.clone(), w.clone())
+                else:
+                    res["identical"] = bool(torch.equal(ref[0], i) and torch.equal(ref[1], j)
+                                            and torch.equal(ref[2], w))
+            res["pairs"] = n
+            res["speedup"] = res["walk"]["ms"] / res["tile"]["ms"]
+            rows[f"{'H*' if dual else 'H'} s={s}"] = res
+    out = {"mode": "core", "metric": "dense-core tile path vs wedge walk, build ms",
+           "m": h.m, "n": h.n, "nnz": h.nnz, "generate_s": gen_s, "builds": rows}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
+    global _ONLY
     args = parse()
+    if args.builds != "all":
+        _ONLY = set()
+        for tok in args.builds.split(","):
+            side, sv = tok.split(":")
+            _ONLY.add((side.strip() == "H*", int(sv)))
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "batch":
+        return run_batch(args)
+    if args.mode == "serve":
+        return run_serve(args)
+    if args.mode == "core":
+        return run_core(args)
     return run_ours(args)
 
 

@@ -145,7 +145,7 @@ def _draw_distinct(sizes: np.ndarray, n: int, rng: np.random.Generator,
     pending = short > 0
     sel = pending[key // n]
     done, work = key[~sel], key[sel]
-    for _ in range(400):
+    for _ in range(50):
         need = np.nonzero(short > 0)[0]
         if need.shape[0] == 0:
             break
@@ -154,8 +154,19 @@ def _draw_distinct(sizes: np.ndarray, n: int, rng: np.random.Generator,
             [work, add_rows * n + draw(add_rows.shape[0])]))
         have = np.bincount(work // n, minlength=m)
         short = np.where(pending, sizes - have, 0)
-    else:  # pragma: no cover - weights too concentrated for the sizes
-        raise RuntimeError("could not draw distinct vertices")
+    # Rows still short (targets close to n under skewed weights: rare, tiny
+    # graphs) take their missing vertices from their complement, uniformly
+    # without replacement.
+    need = np.nonzero(short > 0)[0]
+    if need.shape[0]:
+        extra = []
+        r_all = work // n
+        for row in need:
+            present = work[r_all == row] % n
+            comp = np.setdiff1d(np.arange(n, dtype=np.int64), present)
+            pick = rng.choice(comp, size=int(short[row]), replace=False)
+            extra.append(row * n + pick)
+        work = _unique_sorted(np.concatenate([work] + extra))
     key = np.sort(np.concatenate([done, work]))
     return key // n, key % n
 

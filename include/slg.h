@@ -34,7 +34,8 @@
  * device is reported through a status word that the host reads.
  *
  * Thread safety: calls on different streams may run concurrently from
- * different host threads; the per-device scratch is guarded by a mutex.
+ * different host threads (their kernels overlap on the device); calls with
+ * SLG_ALGO_PLAIN share a per-device scratch and are serialised.
  */
 #ifndef SLG_H_
 #define SLG_H_
@@ -77,6 +78,12 @@ typedef enum slg_status {
                                 (the short-circuit of Section IV-C); the
                                 pair set is unchanged, out_w is not written
                                 and may be NULL */
+#define SLG_TENSOR_CORE 0x4u /* detect a dense core block of the incidence
+                                and count its overlaps on the tensor cores
+                                (slg_tile_overlap); the walk skips the core's
+                                wedges and the tile counts are added before
+                                the threshold, so the result is unchanged.
+                                Binned algorithm only. */
 /* Algorithm selector (mutually exclusive values in bits 8..11). */
 #define SLG_ALGO_MASK 0xF00u
 #define SLG_ALGO_BINNED 0x000u /* default: degree-binned wedge walk */
@@ -165,6 +172,46 @@ int slg_wedges(const slg_hypergraph *h, int32_t s, uint32_t flags,
 int slg_tile_overlap(const uint8_t *A, int32_t rows_pad, int32_t cols_pad,
                      int32_t *C, void *stream);
 
+/*
+ * Batched form: many hypergraphs, each with its own threshold, built by one
+ * pipeline.  The disjoint union of H_1 .. H_k has a block-diagonal incidence
+ * (no vertex is shared), so every pair of its s-line graph lies inside one
+ * member; with each row carrying its member's s_g the union's canonical edge
+ * list is the members' lists, concatenated in member order (Section III
+ * applied member by member).
+ *
+ * slg_plan_create -- builds the union on the device (copies of the members'
+ *   arrays; the members may be freed afterwards), sizes every buffer with one
+ *   counting pass, tunes the row-bin thresholds on this batch (a few timed
+ *   builds) and captures the whole build into a CUDA graph.
+ *     hs     HOST array of `count` hypergraphs whose arrays are device pointers
+ *     s      HOST array of `count` thresholds (>= 1)
+ *     flags  SLG_DUAL, SLG_UNWEIGHTED
+ *     plan   receives the plan (free with slg_plan_destroy)
+ *   Synchronises `stream`.  Errors as for slg_build; SLG_ERR_UNSUPPORTED for
+ *   SLG_TENSOR_CORE or an algorithm flag.
+ * slg_plan_execute -- replays the captured build on `stream`: one graph
+ *   launch, no host synchronisation, results valid when the stream reaches
+ *   that point.
+ * slg_plan_result -- device pointers to the plan's output (owned by the plan;
+ *   ids local to each member, pairs of member g at [offsets[g],
+ *   offsets[g+1])); `offsets` is a HOST array of count + 1 entries (may be
+ *   NULL); reads them synchronously.  Returns the device error status of the
+ *   last execution, if any.
+ * slg_plan_info -- the chosen bin thresholds (warp, CTA small, CTA large
+ *   work limits), the tuned build time in ms and the kernels per execution.
+ */
+typedef struct slg_plan slg_plan;
+int slg_plan_create(const slg_hypergraph *hs, const int32_t *s, int32_t count,
+                    uint32_t flags, slg_plan **plan, void *stream);
+int slg_plan_execute(slg_plan *plan, void *stream);
+int slg_plan_result(const slg_plan *plan, const int32_t **out_i,
+                    const int32_t **out_j, const int32_t **out_w,
+                    int64_t *n_pairs, int64_t *offsets);
+int slg_plan_info(const slg_plan *plan, int32_t *bins, float *tuned_ms,
+                  int32_t *launches);
+int slg_plan_destroy(slg_plan *plan);
+
 /* Statistics of the last call made by this host thread.  Bins: 0 = warp
  * (small rows), 1 = CTA small, 2 = CTA large, 3 = giant rows. */
 typedef struct slg_stats {
@@ -181,9 +228,25 @@ typedef struct slg_stats {
   float ms_walk[4];        /* the walk kernel of each bin */
   float ms_scan;           /* row offsets */
   float ms_gather;         /* output assembly */
+  int64_t core_rows;       /* dense core used by SLG_TENSOR_CORE: rows, */
+  int64_t core_cols;       /* columns and incidences (0 when no core was */
+  int64_t core_nnz;        /* found or the flag was not given) */
+  int64_t giant_cycles[3]; /* giant bin, SM clock cycles summed over CTAs:
+                              walk, partition into buckets, bucket counting */
+  int64_t max_row_work;    /* largest wedge count of one row */
 } slg_stats;
 
 int slg_last_stats(slg_stats *out);
+
+/*
+ * slg_set_core_params -- dense-core selection for SLG_TENSOR_CORE on later
+ * calls from this host thread: core columns have degree >= tau_c, core rows
+ * have >= tau_r incidences in core columns, and the block is used when it
+ * has at least 128 rows, 32 columns and a density >= min_density.
+ * Defaults: 64, 32, 0.02.  Returns SLG_ERR_INVALID for values < 1 or a
+ * density outside (0, 1].
+ */
+int slg_set_core_params(int32_t tau_c, int32_t tau_r, float min_density);
 
 /* Per-phase CUDA-event timing of later calls from this host thread
  * (enable = 1) or not (0, the default).  Events are recorded on the call's

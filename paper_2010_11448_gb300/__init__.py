@@ -21,6 +21,7 @@ import numpy as np
 __all__ = [
     "DeviceHypergraph", "to_device", "count", "build", "build_rows",
     "build_host", "wedges", "last_stats", "set_profiling", "tile_overlap",
+    "set_core_params", "SLG_TENSOR_CORE", "Plan", "alloc_outputs",
     "library_path", "load",
     "SLG_DUAL", "SLG_UNWEIGHTED", "SLG_ALGO_BINNED", "SLG_ALGO_PLAIN",
     "SLG_ALGO_SPGEMM", "SlgError", "ABI_FUNCTIONS",
@@ -28,6 +29,7 @@ __all__ = [
 
 SLG_DUAL = 0x1
 SLG_UNWEIGHTED = 0x2
+SLG_TENSOR_CORE = 0x4
 SLG_ALGO_BINNED = 0x000
 SLG_ALGO_PLAIN = 0x100
 SLG_ALGO_SPGEMM = 0x200
@@ -68,7 +70,12 @@ class _Stats(ctypes.Structure):
                 ("ms_plan", ctypes.c_float),
                 ("ms_walk", ctypes.c_float * 4),
                 ("ms_scan", ctypes.c_float),
-                ("ms_gather", ctypes.c_float)]
+                ("ms_gather", ctypes.c_float),
+                ("core_rows", ctypes.c_int64),
+                ("core_cols", ctypes.c_int64),
+                ("core_nnz", ctypes.c_int64),
+                ("giant_cycles", ctypes.c_int64 * 3),
+                ("max_row_work", ctypes.c_int64)]
 
 
 _I64P = ctypes.POINTER(ctypes.c_int64)
@@ -88,7 +95,17 @@ ABI_FUNCTIONS = {
     "slg_wedges": (ctypes.c_int, [_HP, ctypes.c_int32, ctypes.c_uint32, _I64P, _VP]),
     "slg_last_stats": (ctypes.c_int, [ctypes.POINTER(_Stats)]),
     "slg_set_profiling": (ctypes.c_int, [ctypes.c_int]),
+    "slg_set_core_params": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_float]),
     "slg_tile_overlap": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP]),
+    "slg_plan_create": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, ctypes.c_uint32,
+                                       ctypes.POINTER(ctypes.c_void_p), _VP]),
+    "slg_plan_execute": (ctypes.c_int, [_VP, _VP]),
+    "slg_plan_result": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_void_p),
+                                       ctypes.POINTER(ctypes.c_void_p),
+                                       ctypes.POINTER(ctypes.c_void_p), _I64P, _VP]),
+    "slg_plan_info": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_float),
+                                     ctypes.POINTER(ctypes.c_int32)]),
+    "slg_plan_destroy": (ctypes.c_int, [_VP]),
     "slg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "slg_abi_version": (ctypes.c_int, []),
 }
@@ -158,8 +175,10 @@ def to_device(h, device="cuda") -> DeviceHypergraph:
     return DeviceHypergraph(h.m, h.n, t(h.e_off), t(h.e_idx), t(h.v_off), t(h.v_idx))
 
 
-def _flags(dual, unweighted, algo):
+def _flags(dual, unweighted, algo, tensor=False):
     f = _ALGOS[algo]
+    if tensor:
+        f |= SLG_TENSOR_CORE
     if dual:
         f |= SLG_DUAL
     if unweighted:
@@ -175,14 +194,20 @@ def _stream(stream):
 
 
 def count(h: DeviceHypergraph, s: int, dual=False, unweighted=False,
-          algo="binned", stream=None) -> int:
+          algo="binned", stream=None, tensor=False) -> int:
     """|L_s(H)| (or of H* with dual=True)."""
     n = ctypes.c_int64(0)
-    rc = load().slg_count(ctypes.byref(h.struct), int(s), _flags(dual, unweighted, algo),
+    rc = load().slg_count(ctypes.byref(h.struct), int(s),
+                          _flags(dual, unweighted, algo, tensor),
                           ctypes.byref(n), _stream(stream))
     if rc != 0:
         raise SlgError(rc, "slg_count")
     return int(n.value)
+
+
+def alloc_outputs(capacity, unweighted=False, device="cuda"):
+    """Three int32 device tensors of `capacity` entries for build(out=...)."""
+    return _outputs(capacity, unweighted, device)
 
 
 def _outputs(capacity, unweighted, device):
@@ -195,14 +220,15 @@ def _outputs(capacity, unweighted, device):
 
 
 def build(h: DeviceHypergraph, s: int, dual=False, unweighted=False,
-          algo="binned", capacity=None, out=None, stream=None):
+          algo="binned", capacity=None, out=None, stream=None, tensor=False):
     """The canonical edge list of L_s as int32 tensors (i, j, w); w is None
     with unweighted=True.  Without ``capacity``/``out`` the pair count is
-    taken first with ``count`` (an extra walk)."""
-    flags = _flags(dual, unweighted, algo)
+    taken first with ``count`` (an extra walk).  tensor=True counts a dense
+    core block on the tensor cores (same result)."""
+    flags = _flags(dual, unweighted, algo, tensor)
     if out is None:
         if capacity is None:
-            capacity = count(h, s, dual, unweighted, algo, stream)
+            capacity = count(h, s, dual, unweighted, algo, stream, tensor)
         out = _outputs(capacity, unweighted, h.e_off.device)
     oi, oj, ow = out
     cap = int(oi.shape[0])
@@ -286,7 +312,16 @@ def last_stats() -> dict:
             "incid_bin": list(st.incid_bin), "pairs_bin": list(st.pairs_bin),
             "kernel_launches": st.kernel_launches, "profiled": bool(st.profiled),
             "ms_plan": st.ms_plan, "ms_walk": list(st.ms_walk), "ms_scan": st.ms_scan,
-            "ms_gather": st.ms_gather}
+            "ms_gather": st.ms_gather, "core_rows": st.core_rows, "core_cols": st.core_cols,
+            "core_nnz": st.core_nnz, "giant_cycles": list(st.giant_cycles),
+            "max_row_work": st.max_row_work}
+
+
+def set_core_params(tau_c: int = 64, tau_r: int = 32, min_density: float = 0.02) -> None:
+    """Dense-core selection used by tensor=True on this thread."""
+    rc = load().slg_set_core_params(int(tau_c), int(tau_r), float(min_density))
+    if rc != 0:
+        raise SlgError(rc, "slg_set_core_params")
 
 
 def tile_overlap(A, stream=None):
@@ -301,6 +336,91 @@ def tile_overlap(A, stream=None):
     if rc != 0:
         raise SlgError(rc, "slg_tile_overlap")
     return C
+
+
+class _DeviceInt32:
+    """A device int32 array owned by the library, seen through the CUDA
+    array interface (no copy until .clone())."""
+
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<i4",
+                                         "data": (ptr, False), "version": 3}
+
+
+class Plan:
+    """A batch of hypergraphs (each with its own s) built by one captured
+    pipeline: ``Plan(graphs, s)``, then ``execute()`` (one CUDA-graph launch)
+    and ``results()`` -> list of (i, j, w) tensors per member (member ids)."""
+
+    def __init__(self, graphs, s, dual=False, unweighted=False, stream=None):
+        import torch
+        self._graphs = list(graphs)          # keep device arrays alive
+        self.count = len(self._graphs)
+        arr = (_Hypergraph * self.count)(*[g.struct for g in self._graphs])
+        sv = (ctypes.c_int32 * self.count)(*[int(x) for x in s])
+        self._h = ctypes.c_void_p()
+        self.flags = _flags(dual, unweighted, "binned")
+        self.unweighted = unweighted
+        rc = load().slg_plan_create(ctypes.cast(arr, ctypes.c_void_p),
+                                    ctypes.cast(sv, ctypes.c_void_p), self.count, self.flags,
+                                    ctypes.byref(self._h), _stream(stream))
+        if rc != 0:
+            raise SlgError(rc, "slg_plan_create")
+        self.device = self._graphs[0].e_off.device
+        del torch
+
+    def execute(self, stream=None):
+        rc = load().slg_plan_execute(self._h, _stream(stream))
+        if rc != 0:
+            raise SlgError(rc, "slg_plan_execute")
+
+    def info(self):
+        b = (ctypes.c_int32 * 3)()
+        ms = ctypes.c_float(0)
+        n = ctypes.c_int32(0)
+        load().slg_plan_info(self._h, ctypes.cast(b, ctypes.c_void_p), ctypes.byref(ms),
+                             ctypes.byref(n))
+        return {"bins": list(b), "tuned_ms": ms.value, "launches": n.value}
+
+    def results(self):
+        """Per-member (i, j, w) as int32 CUDA tensors (copies)."""
+        import torch
+        pi, pj, pw = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        n = ctypes.c_int64(0)
+        offs = (ctypes.c_int64 * (self.count + 1))()
+        torch.cuda.synchronize(self.device)
+        rc = load().slg_plan_result(self._h, ctypes.byref(pi), ctypes.byref(pj),
+                                    ctypes.byref(pw), ctypes.byref(n),
+                                    ctypes.cast(offs, ctypes.c_void_p))
+        if rc != 0:
+            raise SlgError(rc, "slg_plan_result")
+        total = int(n.value)
+
+        def view(ptr):
+            if total == 0 or not ptr.value:
+                return None
+            return torch.as_tensor(_DeviceInt32(ptr.value, total), device=self.device).clone()
+        I, J, W = view(pi), view(pj), None if self.unweighted else view(pw)
+        out = []
+        for g in range(self.count):
+            a, b = int(offs[g]), int(offs[g + 1])
+            if I is None:
+                z = torch.zeros(0, dtype=torch.int32, device=self.device)
+                out.append((z, z, None if self.unweighted else z))
+            else:
+                out.append((I[a:b], J[a:b], None if W is None else W[a:b]))
+        return out
+
+    def close(self):
+        if self._h:
+            load().slg_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def set_profiling(enable: bool) -> None:

@@ -1,6 +1,8 @@
 // C ABI of the slg library (declared in include/slg.h): argument checks,
 // per-call working memory, the sequence of planning, walking and output
 // kernels, and the single device->host read of the pair count.
+#include <algorithm>
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -11,20 +13,21 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 
-// Per-device state kept between calls: the giant bin's dense counters (all
-// zero between calls; the kernels restore the zeros they disturb) and a
-// pinned copy of the Meta record.
+// Per-device state kept between calls: the plain kernel's dense counters
+// (all zero between calls; the kernel restores the zeros it disturbs).
 struct DeviceCtx {
-  std::mutex mu;
-  int32_t *giant = nullptr;
+  std::mutex mu;               // one-time set-up; the plain kernel's scratch
+  int32_t *giant = nullptr;    // plain kernel: per-warp zeroed counters
   size_t giant_elems = 0;
-  Meta *meta_host = nullptr;
   bool pool_ready = false;
 };
 
 DeviceCtx g_ctx[kMaxDevices];
 thread_local slg_stats t_stats;
 thread_local int t_profile = 0;
+thread_local int32_t t_tau_c = 64, t_tau_r = 32;
+thread_local Bins t_bins;
+thread_local float t_min_density = 0.02f;
 
 // Events of one profiled call: plan start, walk (kNumBins + 1), scan end,
 // gather end.
@@ -103,7 +106,9 @@ int check_args(const slg_hypergraph *h, int32_t s, uint32_t flags) {
   const uint32_t algo = flags & SLG_ALGO_MASK;
   if (algo != SLG_ALGO_BINNED && algo != SLG_ALGO_PLAIN && algo != SLG_ALGO_SPGEMM)
     return SLG_ERR_UNSUPPORTED;
-  if (flags & ~(uint32_t)(SLG_DUAL | SLG_UNWEIGHTED | SLG_ALGO_MASK)) return SLG_ERR_INVALID;
+  if (flags & ~(uint32_t)(SLG_DUAL | SLG_UNWEIGHTED | SLG_TENSOR_CORE | SLG_ALGO_MASK))
+    return SLG_ERR_INVALID;
+  if ((flags & SLG_TENSOR_CORE) && algo != SLG_ALGO_BINNED) return SLG_ERR_UNSUPPORTED;
   return SLG_OK;
 }
 
@@ -182,7 +187,24 @@ struct Call {
   Work w;
   Events *evs;
   int32_t launches;
+  int64_t core_rows, core_cols, core_nnz;
+  Meta *meta_host;  // this host thread's pinned copy of the device Meta
 };
+
+// One pinned Meta per host thread (calls on different threads and streams
+// run concurrently; each reads its own results).
+cudaError_t thread_meta(Meta **out) {
+  thread_local Meta *m = nullptr;
+  if (!m) {
+    cudaError_t e = cudaMallocHost(&m, sizeof(Meta));
+    if (e != cudaSuccess) {
+      m = nullptr;
+      return e;
+    }
+  }
+  *out = m;
+  return cudaSuccess;
+}
 
 int plain_warps() {
   int dev = 0, sms = 0;
@@ -201,27 +223,28 @@ cudaError_t ensure_scratch(Call &c, size_t *summ_off) {
   return ensure_giant(*c.ctx, counters + pw * (rp >> 10), c.st);
 }
 
-// Per-CTA scratch of the giant bin: 3 ints per wedge of the largest row.
+// Per-CTA scratch of the giant bin: 4 ints per wedge of the largest row.
 cudaError_t giant_scratch(Call &c, int32_t max_work, WalkLaunch *L) {
   L->giant_scratch = nullptr;
   L->giant_stride = 0;
   if (max_work <= 0) return cudaSuccess;
-  const long long stride = 3ll * max_work;
+  const long long stride = 4ll * max_work;
   cudaError_t e = c.pool->get(&L->giant_scratch, (size_t)giant_ctas() * (size_t)stride);
   if (e == cudaSuccess) L->giant_stride = stride;
   return e;
 }
 
 int read_meta(Call &c) {
-  SLG_TRY(cudaMemcpyAsync(c.ctx->meta_host, c.w.meta, sizeof(Meta), cudaMemcpyDeviceToHost, c.st));
+  SLG_TRY(cudaMemcpyAsync(c.meta_host, c.w.meta, sizeof(Meta), cudaMemcpyDeviceToHost, c.st));
   SLG_TRY(cudaStreamSynchronize(c.st));
-  return c.ctx->meta_host->err;
+  return c.meta_host->err;
 }
 
 WalkLaunch walk_launch(Call &c, int mode, int32_t smin, int32_t list_base) {
   WalkLaunch L = {};
   L.a.mode = mode;
   L.a.unweighted = c.unweighted;
+  L.a.row_s = c.sd.row_s;
   L.a.smin = smin;
   L.a.row_begin = list_base;
   L.a.n_e = c.w.n_e;
@@ -230,6 +253,7 @@ WalkLaunch walk_launch(Call &c, int mode, int32_t smin, int32_t list_base) {
   L.a.stage_w = c.w.stage_w;
   L.a.stage_cap = c.w.stage_cap;
   L.a.meta = c.w.meta;
+  L.a.row_work = c.w.row_work;
   L.bin_rows = c.w.bin_rows;
   L.row_work = c.w.row_work;
   L.rows = c.rows;
@@ -237,16 +261,92 @@ WalkLaunch walk_launch(Call &c, int mode, int32_t smin, int32_t list_base) {
   return L;
 }
 
+// Dense core for SLG_TENSOR_CORE: core flags and ranks, a host decision on
+// the block's size and density, the core-excluded column lists, packing and
+// the tensor-core tile counts.  Leaves `core` zero when no block qualifies.
+int plan_core(Call &c, CoreInfo *core) {
+  *core = CoreInfo{};
+  Work &w = c.w;
+  const Side &sd = c.sd;
+  int32_t *core_col, *col_rank, *core_row, *row_rank, *tile;
+  SLG_TRY(c.pool->get(&core_col, (size_t)sd.C + 1));
+  SLG_TRY(c.pool->get(&col_rank, (size_t)sd.C + 1));
+  SLG_TRY(c.pool->get(&core_row, (size_t)sd.R + 1));
+  SLG_TRY(c.pool->get(&row_rank, (size_t)sd.R + 1));
+  const int64_t nt = std::max(xscan_tiles((int64_t)sd.C + 1), xscan_tiles((int64_t)sd.R + 1));
+  SLG_TRY(c.pool->get(&tile, (size_t)nt + 1));
+  SLG_TRY(launch_core_cols(sd, t_tau_c, core_col, w.meta, c.st));
+  SLG_TRY(launch_xscan(core_col, col_rank, (int64_t)sd.C + 1, tile, c.st));
+  SLG_TRY(launch_core_rows(sd, t_tau_r, col_rank, core_row, &w.meta->nnz_core, w.meta, c.st));
+  SLG_TRY(launch_xscan(core_row, row_rank, (int64_t)sd.R + 1, tile, c.st));
+  c.launches += 8;
+  int32_t sizes[2] = {0, 0};
+  SLG_TRY(cudaMemcpyAsync(&sizes[0], row_rank + sd.R, 4, cudaMemcpyDeviceToHost, c.st));
+  SLG_TRY(cudaMemcpyAsync(&sizes[1], col_rank + sd.C, 4, cudaMemcpyDeviceToHost, c.st));
+  int rc = read_meta(c);
+  if (rc) return rc;
+  const int64_t nR = sizes[0], nC = sizes[1];
+  const int64_t nnz_core = (int64_t)c.meta_host->nnz_core;
+  const int32_t kept = c.meta_host->kept;
+  if (nR < 128 || nC < 32 || (double)nnz_core < (double)t_min_density * (double)nR * (double)nC)
+    return SLG_OK;
+  const int64_t Mp = (nR + 127) / 128 * 128, Kp = (nC + 127) / 128 * 128;
+  if (Mp * Kp > (int64_t(1) << 31) || Mp * Mp > (int64_t(1) << 30) || Kp >= (1 << 24))
+    return SLG_OK;  // block too large for the tile path: plain walk
+  int32_t *core_list, *x_cnt, *x_off, *T;
+  uint8_t *A;
+  SLG_TRY(c.pool->get(&core_list, (size_t)nR));
+  SLG_TRY(c.pool->get(&x_cnt, (size_t)nC + 1));
+  SLG_TRY(c.pool->get(&x_off, (size_t)nC + 1));
+  SLG_TRY(launch_core_list(sd.R, row_rank, core_list, c.st));
+  SLG_TRY(cudaMemsetAsync(x_cnt, 0, sizeof(int32_t) * (nC + 1), c.st));
+  SLG_TRY(launch_core_xcount(sd.C, col_rank, w.c_off_s, w.c_idx_s, row_rank, x_cnt, w.meta,
+                             c.st));
+  SLG_TRY(launch_xscan(x_cnt, x_off, nC + 1, tile, c.st));
+  // the core-excluded lists go right after the kept entries (c_idx_s has
+  // room for 2 x nnz entries when the flag is set; they are at most nnz)
+  SLG_TRY(launch_core_xcsc(sd.C, col_rank, w.c_off_s, w.c_idx_s, row_rank, x_off,
+                           w.c_idx_s + kept, w.meta, c.st));
+  SLG_TRY(c.pool->get(&A, (size_t)(Mp * Kp)));
+  SLG_TRY(c.pool->get(&T, (size_t)(Mp * Mp)));
+  void *tasks = nullptr;
+  const int64_t ntile = Mp / 128;
+  SLG_TRY(c.pool->get(reinterpret_cast<int64_t **>(&tasks), (size_t)(ntile * (ntile + 1) / 2)));
+  SLG_TRY(cudaMemsetAsync(A, 0, (size_t)(Mp * Kp), c.st));
+  SLG_TRY(launch_core_pack(sd, row_rank, col_rank, A, (int32_t)Kp, w.meta, c.st));
+  cudaError_t e = launch_tile_overlap(A, (int32_t)Mp, (int32_t)Kp, T, tasks, &w.meta->err, c.st);
+  if (e == cudaErrorNotSupported) return SLG_ERR_UNSUPPORTED;
+  SLG_TRY(e);
+  c.launches += 7;
+  core->row_rank = row_rank;
+  core->col_rank = col_rank;
+  core->x_off = x_off;
+  core->x_base = kept;
+  core->core_list = core_list;
+  core->n_core = (int32_t)nR;
+  core->T = T;
+  core->Mp = (int32_t)Mp;
+  c.core_rows = nR;
+  c.core_cols = nC;
+  c.core_nnz = nnz_core;
+  return SLG_OK;
+}
+
 // Default path: filtered CSC, binned single walk, staging, scan, gather.
 int run_binned(Call &c, int64_t *result) {
   Work &w = c.w;
   SLG_TRY(launch_filter(c.sd, c.smin, w, c.st));
-  SLG_TRY(launch_rows_work(c.sd, c.smin, c.row_begin, c.row_end, w, c.st));
+  CoreInfo core = {};
+  if (c.flags & SLG_TENSOR_CORE) {
+    const int rcc = plan_core(c, &core);
+    if (rcc) return rcc;
+  }
+  SLG_TRY(launch_rows_work(c.sd, c.smin, c.row_begin, c.row_end, w, core, t_bins, c.st));
   c.launches += 4 + (c.rows > 0 ? 1 : 0);
   if (c.op == kOpWedges) {
     int rc = read_meta(c);
     if (rc) return rc;
-    *result = (int64_t)c.ctx->meta_host->wedges;
+    *result = (int64_t)c.meta_host->wedges;
     return SLG_OK;
   }
   if (c.op == kOpBuild && c.capacity > 0) {
@@ -259,15 +359,20 @@ int run_binned(Call &c, int64_t *result) {
   // Planning totals: the giant bin's scratch is sized by its largest row.
   int rc = read_meta(c);
   if (rc) return rc;
-  const int32_t max_giant = c.ctx->meta_host->rows_bin[kBinGiant]
-                                ? c.ctx->meta_host->max_giant_work : 0;
+  // (core rows may have no wedges but still need a giant CTA; their pairs,
+  // staged in the same scratch, also come from up to n_core tile items)
+  const int32_t max_giant = c.meta_host->rows_bin[kBinGiant]
+                                ? std::max(c.meta_host->max_giant_work, (int32_t)1) +
+                                      (core.T ? core.n_core : 0)
+                                : 0;
   WalkLaunch L = walk_launch(c, c.op == kOpBuild ? kStage : kCount, c.smin, c.row_begin);
+  L.a.core = core;
   SLG_TRY(giant_scratch(c, max_giant, &L));
   L.w.r_off = c.sd.r_off;
   L.w.r_idx = c.sd.r_idx;
-  L.w.c_off_s = w.c_off_s;
   L.w.c_idx_s = w.c_idx_s;
   L.w.tail_beg = w.tail_beg;
+  L.w.tail_end = w.tail_end;
   cudaEvent_t *ev = c.evs->on ? c.evs->ev + kEvWalk : nullptr;
   if (c.rows > 0) {
     SLG_TRY(launch_walk(L, c.st, &c.launches, ev));
@@ -279,7 +384,7 @@ int run_binned(Call &c, int64_t *result) {
   c.launches += 3;
   rc = read_meta(c);
   if (rc) return rc;
-  const Meta &m = *c.ctx->meta_host;
+  const Meta &m = *c.meta_host;
   const int64_t pairs = (int64_t)m.pairs;
   *result = pairs;
   if (c.op != kOpBuild) return SLG_OK;
@@ -306,8 +411,11 @@ int run_binned(Call &c, int64_t *result) {
   return rc;
 }
 
-// Plain comparison path: count pass, scan, write pass (two walks).
+// Plain comparison path: count pass, scan, write pass (two walks).  Its
+// per-warp count arrays are a persistent zeroed scratch shared by the
+// device's calls, so plain calls are serialised per device.
 int run_plain(Call &c, int64_t *result) {
+  std::lock_guard<std::mutex> lock(c.ctx->mu);
   Work &w = c.w;
   size_t summ_off = 0;
   SLG_TRY(ensure_scratch(c, &summ_off));
@@ -331,8 +439,8 @@ int run_plain(Call &c, int64_t *result) {
   c.launches += 4;
   int rc = read_meta(c);
   if (rc) return rc;
-  const int64_t pairs = (int64_t)c.ctx->meta_host->pairs;
-  *result = c.op == kOpWedges ? (int64_t)c.ctx->meta_host->wedges : pairs;
+  const int64_t pairs = (int64_t)c.meta_host->pairs;
+  *result = c.op == kOpWedges ? (int64_t)c.meta_host->wedges : pairs;
   if (c.op != kOpBuild) return SLG_OK;
   if (pairs > c.capacity) return SLG_ERR_CAPACITY;
   if (c.evs->on) cudaEventRecord(c.evs->ev[kEvGather0], c.st);
@@ -362,8 +470,8 @@ int run_spgemm(Call &c, int64_t *result) {
   SLG_TRY(c.pool->get(&prefix, (size_t)rows + 1));
   SLG_TRY(c.pool->get(&chunk_ptr, (size_t)rows + 1));
   // 1. product-row sizes (upper bounds: sum of column lengths) and prefix
-  SLG_TRY(launch_rows_full(c.sd, c.row_begin, c.row_end, c.row_begin, w.tail_beg, work, w.n_e,
-                           w.stage_pos, nullptr, rows, w.meta, c.st));
+  SLG_TRY(launch_rows_full(c.sd, c.row_begin, c.row_end, c.row_begin, w.tail_beg, w.tail_end,
+                           work, w.n_e, w.stage_pos, nullptr, rows, w.meta, c.st));
   Work wp = w;
   wp.n_e = work;
   wp.row_ptr = prefix;
@@ -400,14 +508,14 @@ int run_spgemm(Call &c, int64_t *result) {
     while (r1 < rows && pre[r1 + 1] - pre[r0] <= budget) ++r1;
     const int32_t a0 = c.row_begin + r0, a1 = c.row_begin + r1;
     SLG_TRY(cudaMemsetAsync(w.meta, 0, sizeof(Meta), c.st));
-    SLG_TRY(launch_rows_full(c.sd, a0, a1, c.row_begin, w.tail_beg, w.row_work, w.n_e,
-                             w.stage_pos, w.bin_rows, rows, w.meta, c.st));
+    SLG_TRY(launch_rows_full(c.sd, a0, a1, c.row_begin, w.tail_beg, w.tail_end, w.row_work,
+                             w.n_e, w.stage_pos, w.bin_rows, rows, w.meta, c.st));
     WalkLaunch L = Lg;
     L.w.r_off = c.sd.r_off;
     L.w.r_idx = c.sd.r_idx;
-    L.w.c_off_s = c.sd.c_off;
     L.w.c_idx_s = c.sd.c_idx;
     L.w.tail_beg = w.tail_beg;
+    L.w.tail_end = w.tail_end;
     SLG_TRY(launch_walk(L, c.st, &c.launches));
     SLG_TRY(launch_filter_count(a0, a1, c.row_begin, w, c.smin, kept, c.st));
     Work wf = w;
@@ -417,7 +525,7 @@ int run_spgemm(Call &c, int64_t *result) {
     c.launches += 5;
     rc = read_meta(c);
     if (rc) return rc;
-    const Meta &m = *c.ctx->meta_host;
+    const Meta &m = *c.meta_host;
     if (m.stage_overflow) return SLG_ERR_NOMEM;  // cannot happen: chunk fits the budget
     const long long got = (long long)m.pairs;
     products += (long long)m.stage_cursor;
@@ -437,9 +545,9 @@ int run_spgemm(Call &c, int64_t *result) {
   }
   rc = read_meta(c);
   if (rc) return rc;
-  c.ctx->meta_host->pairs = (unsigned long long)total_out;
-  c.ctx->meta_host->wedges = (unsigned long long)total_work;
-  c.ctx->meta_host->stage_cursor = (unsigned long long)products;
+  c.meta_host->pairs = (unsigned long long)total_out;
+  c.meta_host->wedges = (unsigned long long)total_work;
+  c.meta_host->stage_cursor = (unsigned long long)products;
   *result = total_out;
   if (c.op == kOpBuild && total_out > c.capacity) return SLG_ERR_CAPACITY;
   return SLG_OK;
@@ -448,12 +556,14 @@ int run_spgemm(Call &c, int64_t *result) {
 // The whole pipeline for one side, one s and one row range.
 int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin,
         int32_t row_end, Op op, int32_t *out_i, int32_t *out_j, int32_t *out_w,
-        int64_t capacity, int64_t *result, cudaStream_t st) {
+        int64_t capacity, int64_t *result, cudaStream_t st, const int32_t *row_s = nullptr,
+        int32_t *max_row_work = nullptr) {
   int rc = check_args(h, smin, flags);
   if (rc != SLG_OK) return rc;
   if (!result) return SLG_ERR_INVALID;
   Call c = {};
   c.sd = side_of(h, flags);
+  c.sd.row_s = row_s;
   if (row_begin < 0 || row_end < row_begin || row_end > c.sd.R) return SLG_ERR_INVALID;
   c.smin = smin;
   c.flags = flags;
@@ -478,9 +588,11 @@ int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin
 
   int dev = 0;
   DeviceCtx &ctx = ctx_for_current(&dev);
-  std::lock_guard<std::mutex> lock(ctx.mu);
-  ensure_pool(ctx, dev);
-  if (!ctx.meta_host) SLG_TRY(cudaMallocHost(&ctx.meta_host, sizeof(Meta)));
+  {
+    std::lock_guard<std::mutex> lock(ctx.mu);
+    ensure_pool(ctx, dev);
+  }
+  SLG_TRY(thread_meta(&c.meta_host));
   c.ctx = &ctx;
 
   Events evs(t_profile != 0 && op != kOpWedges);
@@ -493,9 +605,10 @@ int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin
   SLG_TRY(pool.get(&w.meta, 1));
   SLG_TRY(pool.get(&w.csr2csc, (size_t)nnz));
   SLG_TRY(pool.get(&w.qs, (size_t)nnz + 1));
-  SLG_TRY(pool.get(&w.c_idx_s, (size_t)nnz));
+  SLG_TRY(pool.get(&w.c_idx_s, (size_t)nnz * ((flags & SLG_TENSOR_CORE) ? 2 : 1) + 1));
   SLG_TRY(pool.get(&w.c_off_s, (size_t)c.sd.C + 1));
   SLG_TRY(pool.get(&w.tail_beg, (size_t)nnz));
+  SLG_TRY(pool.get(&w.tail_end, (size_t)nnz));
   SLG_TRY(pool.get(&w.tile, (size_t)ntiles + 1));
   SLG_TRY(pool.get(&w.bin_rows, (size_t)kNumBins * (c.rows > 0 ? c.rows : 1)));
   SLG_TRY(pool.get(&w.n_e, (size_t)c.rows + 1));
@@ -520,7 +633,7 @@ int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin
   if (rc != SLG_OK) return rc;
 
   slg_stats stats = {};
-  const Meta &m = *ctx.meta_host;
+  const Meta &m = *c.meta_host;
   stats.wedges = (int64_t)m.wedges;
   stats.pairs = op == kOpWedges ? 0 : value;
   stats.rows_active = (int64_t)m.active;
@@ -530,7 +643,13 @@ int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin
     stats.incid_bin[b] = (int64_t)m.incid_bin[b];
     stats.pairs_bin[b] = (int64_t)m.pairs_bin[b];
   }
+  if (max_row_work) *max_row_work = m.max_row_work;
   stats.kernel_launches = c.launches;
+  stats.core_rows = c.core_rows;
+  stats.core_cols = c.core_cols;
+  stats.core_nnz = c.core_nnz;
+  for (int q = 0; q < 3; ++q) stats.giant_cycles[q] = (int64_t)m.giant_cycles[q];
+  stats.max_row_work = m.max_row_work;
   if (evs.on) {
     stats.profiled = 1;
     stats.ms_plan = evs.ms(kEvPlan, kEvWalk);
@@ -540,6 +659,113 @@ int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin
   }
   t_stats = stats;
   return SLG_OK;
+}
+
+
+// ------------------------------------------------------------ batched form --
+
+// Device memory owned by a plan (released by slg_plan_destroy).
+struct Owned {
+  std::vector<void *> ptrs;
+  template <class T>
+  cudaError_t get(T **p, size_t count) {
+    size_t bytes = count * sizeof(T);
+    if (bytes < 16) bytes = 16;
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      return e;
+    }
+    ptrs.push_back(q);
+    *p = static_cast<T *>(q);
+    return cudaSuccess;
+  }
+  ~Owned() {
+    for (void *q : ptrs) cudaFree(q);
+  }
+};
+
+}  // namespace
+}  // namespace slg
+
+struct slg_plan {
+  int dev = 0;
+  uint32_t flags = 0;
+  int32_t count = 0;
+  slg_hypergraph u = {};           // the union (device arrays owned below)
+  slg::Side sd = {};
+  int32_t *row_s_e = nullptr, *row_s_v = nullptr;
+  int32_t *row_base = nullptr;     // [count + 1] first row of each member (side)
+  slg::Work w = {};
+  int32_t *giant = nullptr;
+  long long giant_stride = 0;
+  int32_t *out_i = nullptr, *out_j = nullptr, *out_w = nullptr;
+  long long *offsets = nullptr;    // [count + 1]
+  int64_t pairs = 0;
+  slg::Bins bins;
+  float tuned_ms = 0.f;
+  int32_t launches = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  slg::Owned mem;
+};
+
+namespace slg {
+namespace {
+
+// The whole build of a plan, enqueued without any host synchronisation.
+cudaError_t enqueue_plan(slg_plan *p, const Bins &bins, cudaStream_t st, int32_t *launches) {
+  Work &w = p->w;
+  const Side &sd = p->sd;
+  cudaError_t e = cudaMemsetAsync(w.meta, 0, sizeof(Meta), st);
+  if (e != cudaSuccess) return e;
+  if ((e = launch_validate(sd, w.meta, st)) != cudaSuccess) return e;
+  if ((e = launch_csr2csc(sd, w.csr2csc, w.meta, st)) != cudaSuccess) return e;
+  if ((e = launch_filter(sd, 1, w, st)) != cudaSuccess) return e;
+  if ((e = launch_rows_work(sd, 1, 0, sd.R, w, CoreInfo{}, bins, st)) != cudaSuccess) return e;
+  WalkLaunch L = {};
+  L.w.r_off = sd.r_off;
+  L.w.r_idx = sd.r_idx;
+  L.w.c_idx_s = w.c_idx_s;
+  L.w.tail_beg = w.tail_beg;
+  L.w.tail_end = w.tail_end;
+  L.a.mode = kStage;
+  L.a.unweighted = (p->flags & SLG_UNWEIGHTED) != 0;
+  L.a.row_s = sd.row_s;
+  L.a.smin = 1;
+  L.a.row_begin = 0;
+  L.a.n_e = w.n_e;
+  L.a.stage_pos = w.stage_pos;
+  L.a.stage_j = w.stage_j;
+  L.a.stage_w = w.stage_w;
+  L.a.stage_cap = w.stage_cap;
+  L.a.meta = w.meta;
+  L.a.row_work = w.row_work;
+  L.bin_rows = w.bin_rows;
+  L.row_work = w.row_work;
+  L.rows = sd.R;
+  L.R = sd.R;
+  L.giant_scratch = p->giant;
+  L.giant_stride = p->giant_stride;
+  int32_t n = 0;
+  if (sd.R > 0 && (e = launch_walk(L, st, &n)) != cudaSuccess) return e;
+  if ((e = launch_row_scan(sd.R, w, st)) != cudaSuccess) return e;
+  if (p->pairs > 0) {
+    if ((e = launch_gather(0, sd.R, w, p->out_i, p->out_j, p->out_w, L.a.unweighted, st)) !=
+        cudaSuccess)
+      return e;
+    if ((e = launch_localize(p->out_i, p->out_j, p->pairs, p->row_base, p->count, w.row_ptr,
+                             p->offsets, st)) != cudaSuccess)
+      return e;
+  } else {
+    if ((e = cudaMemsetAsync(p->offsets, 0, sizeof(long long) * (p->count + 1), st)) !=
+        cudaSuccess)
+      return e;
+  }
+  if (launches) *launches = 1 + 2 + 1 + 4 + 1 + n + 3 + 2;
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -650,6 +876,15 @@ int slg_tile_overlap(const uint8_t *A, int32_t rows_pad, int32_t cols_pad, int32
   return h_err ? SLG_ERR_TIMEOUT : SLG_OK;
 }
 
+int slg_set_core_params(int32_t tau_c, int32_t tau_r, float min_density) {
+  if (tau_c < 1 || tau_r < 1 || !(min_density > 0.f && min_density <= 1.f))
+    return SLG_ERR_INVALID;
+  t_tau_c = tau_c;
+  t_tau_r = tau_r;
+  t_min_density = min_density;
+  return SLG_OK;
+}
+
 int slg_set_profiling(int enable) {
   t_profile = enable ? 1 : 0;
   return SLG_OK;
@@ -677,3 +912,205 @@ const char *slg_strerror(int status) {
 int slg_abi_version(void) { return SLG_ABI_VERSION; }
 
 }  // extern "C"
+
+extern "C" int slg_plan_create(const slg_hypergraph *hs, const int32_t *s, int32_t count,
+                               uint32_t flags, slg_plan **plan_out, void *stream) {
+  if (!hs || !s || count < 1 || !plan_out) return SLG_ERR_INVALID;
+  if (flags & ~(uint32_t)(SLG_DUAL | SLG_UNWEIGHTED)) return SLG_ERR_UNSUPPORTED;
+  *plan_out = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t M = 0, N = 0, K = 0, max_len = 0;
+  for (int32_t g = 0; g < count; ++g) {
+    int rc = check_args(&hs[g], s[g], flags);
+    if (rc != SLG_OK) return rc;
+    M += hs[g].n_edges;
+    N += hs[g].n_vertices;
+    K += hs[g].nnz;
+    max_len = std::max<int64_t>(max_len, std::max<int64_t>(hs[g].nnz,
+                                                            std::max(hs[g].n_edges, hs[g].n_vertices)));
+  }
+  if (M >= (int64_t(1) << 31) || N >= (int64_t(1) << 31) || K >= (int64_t(1) << 31))
+    return SLG_ERR_INVALID;
+  std::unique_ptr<slg_plan> p(new slg_plan());
+  cudaGetDevice(&p->dev);
+  p->flags = flags;
+  p->count = count;
+  const bool dual = (flags & SLG_DUAL) != 0;
+  // 1. the union
+  int32_t *e_off, *e_idx, *v_off, *v_idx;
+  SLG_TRY(p->mem.get(&e_off, (size_t)M + 1));
+  SLG_TRY(p->mem.get(&v_off, (size_t)N + 1));
+  SLG_TRY(p->mem.get(&e_idx, (size_t)K));
+  SLG_TRY(p->mem.get(&v_idx, (size_t)K));
+  SLG_TRY(p->mem.get(&p->row_s_e, (size_t)M + 1));
+  SLG_TRY(p->mem.get(&p->row_s_v, (size_t)N + 1));
+  std::vector<BatchGraph> bg((size_t)count);
+  std::vector<int32_t> base((size_t)count + 1);
+  int64_t eb = 0, vb = 0, kb = 0;
+  for (int32_t g = 0; g < count; ++g) {
+    bg[g] = BatchGraph{hs[g].e_off, hs[g].e_idx, hs[g].v_off, hs[g].v_idx, hs[g].n_edges,
+                       hs[g].n_vertices, hs[g].nnz, (int32_t)eb, (int32_t)vb, kb, s[g]};
+    base[g] = (int32_t)(dual ? vb : eb);
+    eb += hs[g].n_edges;
+    vb += hs[g].n_vertices;
+    kb += hs[g].nnz;
+  }
+  base[count] = (int32_t)(dual ? vb : eb);
+  BatchGraph *bg_d;
+  SLG_TRY(p->mem.get(&bg_d, (size_t)count));
+  SLG_TRY(p->mem.get(&p->row_base, (size_t)count + 1));
+  SLG_TRY(cudaMemcpyAsync(bg_d, bg.data(), sizeof(BatchGraph) * count, cudaMemcpyHostToDevice, st));
+  SLG_TRY(cudaMemcpyAsync(p->row_base, base.data(), sizeof(int32_t) * (count + 1),
+                          cudaMemcpyHostToDevice, st));
+  const int32_t tailv[1] = {(int32_t)K};
+  SLG_TRY(cudaMemcpyAsync(e_off + M, tailv, 4, cudaMemcpyHostToDevice, st));
+  SLG_TRY(cudaMemcpyAsync(v_off + N, tailv, 4, cudaMemcpyHostToDevice, st));
+  SLG_TRY(launch_concat(bg_d, count, (int32_t)std::min<int64_t>(max_len, 1 << 30), e_off, e_idx,
+                        v_off, v_idx, p->row_s_e, p->row_s_v, st));
+  SLG_TRY(cudaStreamSynchronize(st));
+  p->u = slg_hypergraph{(int32_t)M, (int32_t)N, K, e_off, e_idx, v_off, v_idx};
+  p->sd = side_of(&p->u, flags);
+  p->sd.row_s = dual ? p->row_s_v : p->row_s_e;
+  // 2. sizes: one counting pass over the union (per-row thresholds)
+  int64_t pairs = 0;
+  int32_t max_work = 0;
+  int rc = run(&p->u, 1, flags, 0, p->sd.R, kOpCount, nullptr, nullptr, nullptr, 0, &pairs, st,
+               p->sd.row_s, &max_work);
+  if (rc != SLG_OK) return rc;
+  p->pairs = pairs;
+  // 3. persistent buffers
+  Work &w = p->w;
+  const int64_t nnz = K, R = p->sd.R;
+  SLG_TRY(p->mem.get(&w.meta, 1));
+  SLG_TRY(p->mem.get(&w.csr2csc, (size_t)nnz));
+  SLG_TRY(p->mem.get(&w.qs, (size_t)nnz + 1));
+  SLG_TRY(p->mem.get(&w.c_idx_s, (size_t)nnz + 1));
+  SLG_TRY(p->mem.get(&w.c_off_s, (size_t)p->sd.C + 1));
+  SLG_TRY(p->mem.get(&w.tail_beg, (size_t)nnz));
+  SLG_TRY(p->mem.get(&w.tail_end, (size_t)nnz));
+  SLG_TRY(p->mem.get(&w.tile, (size_t)((nnz + 4095) / 4096) + 1));
+  SLG_TRY(p->mem.get(&w.bin_rows, (size_t)kNumBins * (R > 0 ? R : 1)));
+  SLG_TRY(p->mem.get(&w.n_e, (size_t)R + 1));
+  SLG_TRY(p->mem.get(&w.row_work, (size_t)R + 1));
+  SLG_TRY(p->mem.get(&w.stage_pos, (size_t)R + 1));
+  SLG_TRY(p->mem.get(&w.row_ptr, (size_t)R + 1));
+  SLG_TRY(p->mem.get(&w.tile64, (size_t)((R + 4095) / 4096) + 1));
+  SLG_TRY(p->mem.get(&w.stage_j, (size_t)std::max<int64_t>(pairs, 1)));
+  SLG_TRY(p->mem.get(&w.stage_w, (size_t)std::max<int64_t>(pairs, 1)));
+  w.stage_cap = pairs;
+  SLG_TRY(p->mem.get(&p->out_i, (size_t)std::max<int64_t>(pairs, 1)));
+  SLG_TRY(p->mem.get(&p->out_j, (size_t)std::max<int64_t>(pairs, 1)));
+  SLG_TRY(p->mem.get(&p->out_w, (size_t)std::max<int64_t>(pairs, 1)));
+  SLG_TRY(p->mem.get(&p->offsets, (size_t)count + 1));
+  if (max_work > 0) {
+    p->giant_stride = 4ll * max_work;
+    SLG_TRY(p->mem.get(&p->giant, (size_t)giant_ctas() * (size_t)p->giant_stride));
+  }
+  // 4. autotuner: bin thresholds, timed on this batch
+  const Bins cands[] = {Bins{}, Bins{64, 1024, 4096}, Bins{128, 512, 4096}, Bins{128, 1024, 2048},
+                        Bins{32, 512, 2048}, Bins{128, 256, 4096}};
+  cudaEvent_t t0, t1;
+  SLG_TRY(cudaEventCreate(&t0));
+  SLG_TRY(cudaEventCreate(&t1));
+  float best = 1e30f;
+  Bins best_bins;
+  for (const Bins &b : cands) {
+    if (b.warp > kWarpMaxWork || b.ctas > kCtaSMaxWork || b.ctal > kCtaLMaxWork) continue;
+    if (!p->giant && p->sd.R > 0 && max_work > b.ctal) continue;
+    float ms = 0.f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(t0, st);
+      cudaError_t e = enqueue_plan(p.get(), b, st, nullptr);
+      cudaEventRecord(t1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+      if (e != cudaSuccess) {
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+        cudaGetLastError();
+        return status_of(e);
+      }
+      float t = 0.f;
+      cudaEventElapsedTime(&t, t0, t1);
+      if (rep > 0) ms += t;  // first repetition warms up
+    }
+    if (ms < best) {
+      best = ms;
+      best_bins = b;
+    }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  p->bins = best_bins;
+  p->tuned_ms = best / 2.f;
+  // 5. capture the tuned build into a CUDA graph
+  cudaStream_t cs;
+  SLG_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e2 = enqueue_plan(p.get(), p->bins, cs, &p->launches);
+    e = cudaStreamEndCapture(cs, &p->graph);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    return status_of(e);
+  }
+  *plan_out = p.release();
+  return SLG_OK;
+}
+
+extern "C" int slg_plan_execute(slg_plan *p, void *stream) {
+  if (!p || !p->exec) return SLG_ERR_INVALID;
+  cudaError_t e = cudaGraphLaunch(p->exec, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return status_of(e);
+  }
+  return SLG_OK;
+}
+
+extern "C" int slg_plan_result(const slg_plan *p, const int32_t **out_i, const int32_t **out_j,
+                               const int32_t **out_w, int64_t *n_pairs, int64_t *offsets) {
+  if (!p) return SLG_ERR_INVALID;
+  if (out_i) *out_i = p->out_i;
+  if (out_j) *out_j = p->out_j;
+  if (out_w) *out_w = (p->flags & SLG_UNWEIGHTED) ? nullptr : p->out_w;
+  if (n_pairs) *n_pairs = p->pairs;
+  if (offsets) {
+    int32_t err = 0;
+    cudaError_t e = cudaMemcpy(offsets, p->offsets, sizeof(long long) * (p->count + 1),
+                               cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&err, &p->w.meta->err, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return status_of(e);
+    }
+    if (err) return err;
+  }
+  return SLG_OK;
+}
+
+extern "C" int slg_plan_info(const slg_plan *p, int32_t *bins, float *tuned_ms,
+                             int32_t *launches) {
+  if (!p) return SLG_ERR_INVALID;
+  if (bins) {
+    bins[0] = p->bins.warp;
+    bins[1] = p->bins.ctas;
+    bins[2] = p->bins.ctal;
+  }
+  if (tuned_ms) *tuned_ms = p->tuned_ms;
+  if (launches) *launches = p->launches;
+  return SLG_OK;
+}
+
+extern "C" int slg_plan_destroy(slg_plan *p) {
+  if (!p) return SLG_OK;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  delete p;
+  return SLG_OK;
+}

@@ -27,7 +27,7 @@ enum Bin : int { kBinWarp = 0, kBinCtaS = 1, kBinCtaL = 2, kBinGiant = 3, kNumBi
 // neighbours <= wedges).
 constexpr int32_t kWarpMaxWork = 128;
 constexpr int32_t kCtaSMaxWork = 1024;
-constexpr int32_t kCtaLMaxWork = 8192;
+constexpr int32_t kCtaLMaxWork = 4096;
 
 // Counters the device writes and the host reads once per call.
 struct Meta {
@@ -45,6 +45,9 @@ struct Meta {
   unsigned int giant_ticket;           // dynamic giant-row scheduling
   int32_t kept;                        // entries of the filtered CSC
   int32_t max_giant_work;              // largest work of a giant-bin row
+  unsigned long long nnz_core;         // incidences of the dense core
+  int32_t max_row_work;                // largest work of any row
+  unsigned long long giant_cycles[4];  // giant bin: SM cycles in walk, partition, buckets
 };
 
 // Where a device-side check fired (for error reports).
@@ -152,22 +155,26 @@ __device__ __forceinline__ uint32_t hash_slot(int32_t f, uint32_t T) {
 
 struct Walk {
   const int32_t *r_off, *r_idx;      // CSR of the side
-  const int32_t *c_off_s, *c_idx_s;  // CSC filtered to rows of size >= s
-  const int32_t *tail_beg;           // per CSR incidence of an active row
+  const int32_t *c_idx_s;            // far ends: CSC filtered to rows of size >= s
+  const int32_t *tail_beg;           // per CSR incidence: its tail [beg, end)
+  const int32_t *tail_end;
 };
 
 // CTA-wide walker.  Shared scratch: s_beg[NT], s_pref[NT + 1], ws[NT/32 + 1].
+// fn(f, i) receives every wedge's far end f and its index i in the row's
+// flattened wedge list (0 .. work-1).  Each thread takes G consecutive
+// wedges per step, found by one binary search over the prefix sums.
 template <int NT, int G, class Fn>
 __device__ __forceinline__ void cta_walk(const Walk &w, int32_t k0, int32_t k1,
                                          int32_t *s_beg, int32_t *s_pref, int32_t *ws,
                                          Fn &&fn) {
+  int32_t done = 0;  // wedges of earlier batches
   for (int32_t base = k0; base < k1; base += NT) {
     const int32_t k = base + (int32_t)threadIdx.x;
     int32_t b = 0, len = 0;
     if (k < k1) {
-      const int32_t v = __ldg(w.r_idx + k);
       b = __ldg(w.tail_beg + k);
-      len = __ldg(w.c_off_s + v + 1) - b;
+      len = __ldg(w.tail_end + k) - b;
     }
     int32_t total;
     const int32_t inc = block_inclusive_scan<NT>(len, ws, &total);
@@ -182,50 +189,27 @@ __device__ __forceinline__ void cta_walk(const Walk &w, int32_t k0, int32_t k1,
         if (s_pref[mid] <= i0) lo = mid;
         else hi = mid;
       }
+      // positions first, then the G loads (independent, all in flight)
+      int32_t src[G];
       int32_t j = lo;
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         const int32_t i = i0 + g;
+        src[g] = -1;
         if (i < total) {
           while (s_pref[j + 1] <= i) ++j;
-          fn(__ldg(w.c_idx_s + s_beg[j] + (i - s_pref[j])));
+          src[g] = s_beg[j] + (i - s_pref[j]);
         }
       }
-    }
-    __syncthreads();
-  }
-}
-
-// Warp-wide walker for small rows (no shared memory; shuffles only).
-template <class Fn>
-__device__ __forceinline__ void warp_walk(const Walk &w, int32_t k0, int32_t k1, Fn &&fn) {
-  const int lane = threadIdx.x & 31;
-  for (int32_t base = k0; base < k1; base += 32) {
-    const int32_t k = base + lane;
-    int32_t b = 0, len = 0;
-    if (k < k1) {
-      const int32_t v = __ldg(w.r_idx + k);
-      b = __ldg(w.tail_beg + k);
-      len = __ldg(w.c_off_s + v + 1) - b;
-    }
-    const int32_t inc = warp_inclusive_scan(len);
-    const int32_t total = __shfl_sync(0xffffffffu, inc, 31);
-    for (int32_t i0 = 0; i0 < total; i0 += 32) {
-      const int32_t i = i0 + lane;
-      // j = number of incidences whose tail ends at or before i
-      int32_t j = 0;
+      int32_t f[G];
 #pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const int32_t cand = j + step;
-        const int32_t end = __shfl_sync(0xffffffffu, inc, cand - 1);
-        if (end <= i) j = cand;
-      }
-      const int32_t jj = j < 31 ? j : 31;
-      const int32_t seg_inc = __shfl_sync(0xffffffffu, inc, jj);
-      const int32_t seg_len = __shfl_sync(0xffffffffu, len, jj);
-      const int32_t seg_beg = __shfl_sync(0xffffffffu, b, jj);
-      if (i < total) fn(__ldg(w.c_idx_s + seg_beg + (i - (seg_inc - seg_len))));
+      for (int g = 0; g < G; ++g) f[g] = src[g] >= 0 ? __ldg(w.c_idx_s + src[g]) : -1;
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+        if (src[g] >= 0) fn(f[g], done + i0 + g);
     }
+    done += total;
+    __syncthreads();
   }
 }
 
@@ -236,6 +220,34 @@ struct Side {
   int32_t R, C;     // rows (hyperedges of the side), columns (its vertices)
   int64_t nnz;
   const int32_t *r_off, *r_idx, *c_off, *c_idx;
+  const int32_t *row_s = nullptr;  // per-row threshold (batched form), else null
+};
+
+// Threshold of row e: its own (batched form) or the call's s.
+__device__ __forceinline__ int32_t s_of(const int32_t *row_s, int32_t smin, int32_t e) {
+  return row_s ? __ldg(row_s + e) : smin;
+}
+
+// Wedge-work thresholds of the bins (runtime; each at most the capacity the
+// bin's kernel is compiled for: kWarpMaxWork, kCtaSMaxWork, kCtaLMaxWork).
+struct Bins {
+  int32_t warp = kWarpMaxWork, ctas = kCtaSMaxWork, ctal = kCtaLMaxWork;
+};
+
+// Dense core for the tensor-core tile path (all null / 0 when unused).
+// Core rows form an ascending list; row_rank / col_rank are exclusive scans
+// of the core flags (rank[x+1] != rank[x] marks a core member).  For core
+// columns, the entries of the filtered CSC that are not core rows are stored
+// at c_idx_s[x_base + x_off[rank] .. x_base + x_off[rank + 1]).  T holds the
+// tile counts |e ∩ f ∩ C_c| of core rows, row-major with stride Mp.
+struct CoreInfo {
+  const int32_t *row_rank, *col_rank;
+  const int32_t *x_off;
+  int32_t x_base;
+  const int32_t *core_list;
+  int32_t n_core;
+  const int32_t *T;
+  int32_t Mp;
 };
 
 // Per-call device buffers (carved out of one pool allocation).
@@ -244,7 +256,8 @@ struct Work {
   int32_t *qs;         // [nnz + 1] exclusive scan of "row of this CSC entry kept"
   int32_t *c_idx_s;    // [nnz] filtered CSC ids
   int32_t *c_off_s;    // [C + 1] filtered CSC offsets
-  int32_t *tail_beg;   // [nnz]
+  int32_t *tail_beg;   // [nnz] tail of each incidence: [tail_beg, tail_end)
+  int32_t *tail_end;   // [nnz]
   int32_t *tile;       // [ntiles + 1] scan scratch
   int32_t *bin_rows;   // [kNumBins][R] row lists
   int32_t *n_e;        // [R] pairs per row
@@ -261,7 +274,29 @@ cudaError_t launch_validate(const Side &s, Meta *meta, cudaStream_t st);
 cudaError_t launch_csr2csc(const Side &s, int32_t *csr2csc, Meta *meta, cudaStream_t st);
 cudaError_t launch_filter(const Side &s, int32_t smin, const Work &w, cudaStream_t st);
 cudaError_t launch_rows_work(const Side &s, int32_t smin, int32_t row_begin, int32_t row_end,
-                             const Work &w, cudaStream_t st);
+                             const Work &w, const CoreInfo &core, const Bins &bins,
+                             cudaStream_t st);
+
+// Dense-core detection / packing (slg_core.cu).
+int64_t xscan_tiles(int64_t n);
+cudaError_t launch_xscan(const int32_t *in, int32_t *out, int64_t n, int32_t *tile,
+                         cudaStream_t st);
+cudaError_t launch_core_cols(const Side &s, int32_t tau_c, int32_t *core_col, const Meta *meta,
+                             cudaStream_t st);
+cudaError_t launch_core_rows(const Side &s, int32_t tau_r, const int32_t *col_rank,
+                             int32_t *core_row, unsigned long long *nnz_core, const Meta *meta,
+                             cudaStream_t st);
+cudaError_t launch_core_list(int32_t R, const int32_t *row_rank, int32_t *core_list,
+                             cudaStream_t st);
+cudaError_t launch_core_pack(const Side &s, const int32_t *row_rank, const int32_t *col_rank,
+                             uint8_t *A, int32_t Kp, const Meta *meta, cudaStream_t st);
+cudaError_t launch_core_xcount(int32_t C, const int32_t *col_rank, const int32_t *c_off_s,
+                               const int32_t *c_idx_s, const int32_t *row_rank, int32_t *x_cnt,
+                               const Meta *meta, cudaStream_t st);
+cudaError_t launch_core_xcsc(int32_t C, const int32_t *col_rank, const int32_t *c_off_s,
+                             const int32_t *c_idx_s, const int32_t *row_rank,
+                             const int32_t *x_off, int32_t *x_idx, const Meta *meta,
+                             cudaStream_t st);
 // Output modes of the walk: COUNT (pairs per row only), STAGE (each row's
 // sorted pairs appended to a staging area at an atomically reserved offset),
 // DIRECT (written to their final place; row_ptr known).
@@ -270,7 +305,10 @@ enum Mode : int { kCount = 0, kStage = 1, kDirect = 2 };
 struct EmitArgs {
   int mode;
   int unweighted;
+  const int32_t *row_s;               // per-row threshold, or null: smin
   int full_rows;                      // 1: tails are whole columns, far ends in [0, R)
+  const int32_t *row_work;            // [rows] wedges per row (giant bin)
+  CoreInfo core;                      // dense core (tile counts added by the giant bin)
   int32_t smin;
   int32_t row_begin;
   int32_t *n_e;                       // [rows] pairs per row
@@ -288,7 +326,7 @@ struct WalkLaunch {
   const int32_t *bin_rows;  // [kNumBins][rows] row lists
   const int32_t *row_work;  // [rows] wedges per row
   int32_t rows;             // rows in the range (list stride)
-  int32_t *giant_scratch;   // [giant_ctas][3 * max giant work] wedge ends + pairs
+  int32_t *giant_scratch;   // [giant_ctas][4 * max giant work] wedge ends + pairs
   long long giant_stride;   // ints per giant CTA
   int32_t R;                // rows of the side (far ends lie in [0, R))
 };
@@ -304,6 +342,22 @@ cudaError_t launch_walk(const WalkLaunch &L, cudaStream_t st, int32_t *launches,
 cudaError_t launch_row_scan(int32_t rows, const Work &w, cudaStream_t st);
 cudaError_t launch_gather(int32_t row_begin, int32_t rows, const Work &w, int32_t *out_i,
                           int32_t *out_j, int32_t *out_w, int unweighted, cudaStream_t st);
+
+// Batched form (slg_plan.cu): union of many hypergraphs.
+struct BatchGraph {            // one member, device pointers
+  const int32_t *e_off, *e_idx, *v_off, *v_idx;
+  int32_t m, n;
+  int64_t nnz;
+  int32_t e_base, v_base;      // id offsets in the union
+  int64_t k_base;              // incidence offset in the union
+  int32_t s;
+};
+cudaError_t launch_concat(const BatchGraph *g, int32_t count, int32_t max_len, int32_t *e_off,
+                          int32_t *e_idx, int32_t *v_off, int32_t *v_idx, int32_t *row_s_e,
+                          int32_t *row_s_v, cudaStream_t st);
+cudaError_t launch_localize(int32_t *out_i, int32_t *out_j, long long pairs,
+                            const int32_t *row_base, int32_t count, const long long *row_ptr,
+                            long long *offsets, cudaStream_t st);
 
 int giant_ctas_for_device();
 
@@ -322,7 +376,8 @@ size_t tile_overlap_smem();
 
 // Filtered SpGEMM comparison: full-column tails / per-row work, filtration.
 cudaError_t launch_rows_full(const Side &sd, int32_t row_begin, int32_t row_end,
-                             int32_t list_base, int32_t *tail_beg, int32_t *work_out,
+                             int32_t list_base, int32_t *tail_beg, int32_t *tail_end,
+                             int32_t *work_out,
                              int32_t *n_e, long long *stage_pos, int32_t *bin_rows,
                              int32_t list_stride, Meta *meta, cudaStream_t st);
 cudaError_t launch_filter_count(int32_t row_begin, int32_t row_end, int32_t list_base,

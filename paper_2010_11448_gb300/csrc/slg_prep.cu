@@ -72,7 +72,7 @@ constexpr int kScanTile = kScanNT * kScanIPT;   // 4096 CSC entries per tile
 
 __device__ __forceinline__ int32_t kept(const Side &s, int32_t q, int32_t smin) {
   const int32_t f = __ldg(s.c_idx + q);
-  return (__ldg(s.r_off + f + 1) - __ldg(s.r_off + f)) >= smin;
+  return (__ldg(s.r_off + f + 1) - __ldg(s.r_off + f)) >= s_of(s.row_s, smin, f);
 }
 
 __global__ __launch_bounds__(kScanNT) void k_filter_reduce(Side s, int32_t smin,
@@ -134,7 +134,7 @@ __global__ __launch_bounds__(kScanNT) void k_filter_scatter(Side s, int32_t smin
     int32_t k = 0, f = 0;
     if (q < s.nnz) {
       f = __ldg(s.c_idx + q);
-      k = (__ldg(s.r_off + f + 1) - __ldg(s.r_off + f)) >= smin;
+      k = (__ldg(s.r_off + f + 1) - __ldg(s.r_off + f)) >= s_of(s.row_s, smin, f);
     }
     int32_t total;
     const int32_t inc = block_inclusive_scan<kScanNT>(k, ws, &total);
@@ -162,10 +162,10 @@ __global__ void k_filter_offsets(Side s, const int32_t *__restrict__ qs,
 constexpr int kRowsNT = 256;
 constexpr int kRowsPerBlock = 64;
 
-__device__ __forceinline__ int bin_of(int32_t work) {
-  if (work <= kWarpMaxWork) return kBinWarp;
-  if (work <= kCtaSMaxWork) return kBinCtaS;
-  if (work <= kCtaLMaxWork) return kBinCtaL;
+__device__ __forceinline__ int bin_of(int32_t work, const Bins &b) {
+  if (work <= b.warp) return kBinWarp;
+  if (work <= b.ctas) return kBinCtaS;
+  if (work <= b.ctal) return kBinCtaL;
   return kBinGiant;
 }
 
@@ -180,7 +180,10 @@ __global__ __launch_bounds__(kRowsNT) void k_rows_work(Side s, int32_t smin, int
                                                        const int32_t *__restrict__ csr2csc,
                                                        const int32_t *__restrict__ qs,
                                                        const int32_t *__restrict__ c_off_s,
+                                                       const int32_t *__restrict__ c_idx_s,
+                                                       CoreInfo core, Bins bins,
                                                        int32_t *__restrict__ tail_beg,
+                                                       int32_t *__restrict__ tail_end,
                                                        int32_t *__restrict__ n_e,
                                                        long long *__restrict__ stage_pos,
                                                        int32_t *__restrict__ row_work,
@@ -202,12 +205,30 @@ __global__ __launch_bounds__(kRowsNT) void k_rows_work(Side s, int32_t smin, int
     int32_t work = 0;
     if (e < row_end) {
       const int32_t lo = s.r_off[e], hi = s.r_off[e + 1];
-      if (hi - lo >= smin) {
+      const bool core_row = core.row_rank && core.row_rank[e + 1] != core.row_rank[e];
+      if (hi - lo >= s_of(s.row_s, smin, e)) {
         for (int32_t k = lo + lane; k < hi; k += 32) {
           const int32_t v = s.r_idx[k];
-          const int32_t tb = qs[csr2csc[k]] + 1;
+          int32_t tb, te;
+          if (core_row && core.col_rank[v + 1] != core.col_rank[v]) {
+            // core row at a core column: its tail skips the core rows (their
+            // shared core vertices are counted on the tensor cores)
+            const int32_t cv = core.col_rank[v];
+            int32_t a = core.x_base + core.x_off[cv], b = core.x_base + core.x_off[cv + 1];
+            te = b;
+            while (a < b) {  // first entry > e
+              const int32_t mid = (a + b) >> 1;
+              if (c_idx_s[mid] <= e) a = mid + 1;
+              else b = mid;
+            }
+            tb = a;
+          } else {
+            tb = qs[csr2csc[k]] + 1;
+            te = c_off_s[v + 1];
+          }
           tail_beg[k] = tb;
-          work += c_off_s[v + 1] - tb;
+          tail_end[k] = te;
+          work += te - tb;
         }
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) work += __shfl_xor_sync(0xffffffffu, work, d);
@@ -216,17 +237,26 @@ __global__ __launch_bounds__(kRowsNT) void k_rows_work(Side s, int32_t smin, int
         n_e[e - row_begin] = 0;
         stage_pos[e - row_begin] = -1;
         row_work[e - row_begin] = work;
+        if (work) atomicMax(&meta->max_row_work, work);
       }
     }
-    if (lane == 0) s_work[i] = (e < row_end) ? work : 0;
+    if (lane == 0) {
+      // core rows always go to the giant bin (it adds their tile counts),
+      // marked by a negative work entry here
+      const bool core_row = e < row_end && core.row_rank && core.row_rank[e + 1] != core.row_rank[e] &&
+                            s.r_off[e + 1] - s.r_off[e] >= s_of(s.row_s, smin, e);
+      s_work[i] = (e < row_end) ? (core_row ? -1 - work : work) : 0;
+    }
   }
   __syncthreads();
   int my_bin = -1, my_slot = 0;
   int32_t my_work = 0;
   if (threadIdx.x < kRowsPerBlock) {
     my_work = s_work[threadIdx.x];
-    if (my_work > 0) {
-      my_bin = bin_of(my_work);
+    const bool forced = my_work < 0;
+    if (forced) my_work = -1 - my_work;
+    if (my_work > 0 || forced) {
+      my_bin = forced ? (int)kBinGiant : bin_of(my_work, bins);
       if (my_bin == kBinGiant) atomicMax(&meta->max_giant_work, my_work);
       my_slot = atomicAdd(&s_cnt[my_bin], 1);
       atomicAdd(&s_w[my_bin], (unsigned long long)my_work);
@@ -248,7 +278,7 @@ __global__ __launch_bounds__(kRowsNT) void k_rows_work(Side s, int32_t smin, int
     int act = 0;
     for (int i = 0; i < kRowsPerBlock; ++i) {
       const int32_t e = r0 + i;
-      if (e < row_end && s.r_off[e + 1] - s.r_off[e] >= smin) ++act;
+      if (e < row_end && s.r_off[e + 1] - s.r_off[e] >= s_of(s.row_s, smin, e)) ++act;
     }
     if (act) atomicAdd(&meta->active, (unsigned long long)act);
   }
@@ -295,12 +325,15 @@ cudaError_t launch_filter(const Side &s, int32_t smin, const Work &w, cudaStream
 }
 
 cudaError_t launch_rows_work(const Side &s, int32_t smin, int32_t row_begin, int32_t row_end,
-                             const Work &w, cudaStream_t st) {
+                             const Work &w, const CoreInfo &core, const Bins &bins,
+                             cudaStream_t st) {
   const int32_t rows = row_end - row_begin;
   if (rows <= 0) return cudaSuccess;
   const int grid = (rows + kRowsPerBlock - 1) / kRowsPerBlock;
   k_rows_work<<<grid, kRowsNT, 0, st>>>(s, smin, row_begin, row_end, w.csr2csc, w.qs, w.c_off_s,
-                                        w.tail_beg, w.n_e, w.stage_pos, w.row_work, w.bin_rows,
+                                        w.c_idx_s, core, bins,
+                                        w.tail_beg, w.tail_end, w.n_e, w.stage_pos, w.row_work,
+                                        w.bin_rows,
                                         w.meta);
   return cudaGetLastError();
 }

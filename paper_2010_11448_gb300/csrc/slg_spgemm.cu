@@ -27,6 +27,7 @@ __device__ __forceinline__ int bin_of_full(int32_t work) {
 __global__ __launch_bounds__(kNT) void k_rows_full(Side s, int32_t row_begin, int32_t row_end,
                                                    int32_t list_base,
                                                    int32_t *__restrict__ tail_beg,
+                                                   int32_t *__restrict__ tail_end,
                                                    int32_t *__restrict__ work_out,
                                                    int32_t *__restrict__ n_e,
                                                    long long *__restrict__ stage_pos,
@@ -45,9 +46,12 @@ __global__ __launch_bounds__(kNT) void k_rows_full(Side s, int32_t row_begin, in
       const int32_t lo = s.r_off[e], hi = s.r_off[e + 1];
       for (int32_t k = lo + lane; k < hi; k += 32) {
         const int32_t v = s.r_idx[k];
-        const int32_t cb = s.c_off[v];
-        if (bin_rows) tail_beg[k] = cb;
-        work += s.c_off[v + 1] - cb;
+        const int32_t cb = s.c_off[v], ce = s.c_off[v + 1];
+        if (bin_rows) {
+          tail_beg[k] = cb;
+          tail_end[k] = ce;
+        }
+        work += ce - cb;
       }
 #pragma unroll
       for (int d = 16; d > 0; d >>= 1) work += __shfl_xor_sync(0xffffffffu, work, d);
@@ -164,12 +168,14 @@ int grid_warps(int32_t rows) {
 }  // namespace
 
 cudaError_t launch_rows_full(const Side &sd, int32_t row_begin, int32_t row_end,
-                             int32_t list_base, int32_t *tail_beg, int32_t *work_out,
+                             int32_t list_base, int32_t *tail_beg, int32_t *tail_end,
+                             int32_t *work_out,
                              int32_t *n_e, long long *stage_pos, int32_t *bin_rows,
                              int32_t list_stride, Meta *meta, cudaStream_t st) {
   if (row_end <= row_begin) return cudaSuccess;
   k_rows_full<<<grid_rows(row_end - row_begin), kNT, 0, st>>>(sd, row_begin, row_end, list_base,
-                                                              tail_beg, work_out, n_e, stage_pos,
+                                                              tail_beg, tail_end, work_out, n_e,
+                                                              stage_pos,
                                                               bin_rows, list_stride, meta);
   return cudaGetLastError();
 }

@@ -187,11 +187,11 @@ __global__ __launch_bounds__(128, 1) void k_tile_overlap(const __grid_constant__
       }
     }
     mma_commit(done);
-    if (!ok) atomicExch(err, 1);
+    if (!ok) atomicExch(err, (int32_t)SLG_ERR_TIMEOUT);
   }
   __syncwarp();
   // everyone waits for the accumulator (bounded)
-  if (!mbar_wait(done, 0)) atomicExch(err, 1);
+  if (!mbar_wait(done, 0)) atomicExch(err, (int32_t)SLG_ERR_TIMEOUT);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (*(volatile int32_t *)err == 0) {
     const int32_t row = t.bi * kTcTile + warp * 32 + lane;

@@ -10,15 +10,16 @@
 //                               addressing table holding twice the row's work
 //                               (it can never fill), then sorts the surviving
 //                               pairs in shared memory;
-//   giant bin  (work > 8192):   a CTA counts in a dense per-CTA array in
-//                               global memory (the paper's per-thread visited
-//                               array, holding counts) and marks touched
-//                               groups of 32 counters in a shared bitmap;
-//                               scanning the bitmap in order emits sorted.
+//   giant bin  (work > 8192):   a CTA splits the row's far ends into f-range
+//                               buckets through a per-CTA global scratch and
+//                               counts each bucket, in ascending f, in the
+//                               shared-memory table.
 //
 // Output modes: COUNT (pairs per row only), STAGE (each row's sorted pairs
 // are appended to a staging area at an atomically reserved offset) and
 // DIRECT (written to their final place, row_ptr known).
+#include <mutex>
+
 #include "slg_internal.cuh"
 
 namespace slg {
@@ -70,15 +71,15 @@ __global__ __launch_bounds__(kWarpNT) void k_walk_warp(Walk w, const int32_t *__
   for (long long r = gw; r < nrows; r += nw) {
     const int32_t e = rows[r];
     const int32_t k0 = w.r_off[e], k1 = w.r_off[e + 1];
+    const int32_t smin = s_of(a.row_s, a.smin, e);
     // 1. gather the wedge ends (row work <= kWarpBuf by binning)
     int32_t filled = 0;
     for (int32_t base = k0; base < k1; base += 32) {
       const int32_t k = base + lane;
       int32_t b = 0, len = 0;
       if (k < k1) {
-        const int32_t v = __ldg(w.r_idx + k);
         b = __ldg(w.tail_beg + k);
-        len = __ldg(w.c_off_s + v + 1) - b;
+        len = __ldg(w.tail_end + k) - b;
       }
       const int32_t inc = warp_inclusive_scan(len);
       const int32_t total = __shfl_sync(0xffffffffu, inc, 31);
@@ -128,7 +129,7 @@ __global__ __launch_bounds__(kWarpNT) void k_walk_warp(Walk w, const int32_t *__
       if (p < n && (p == 0 || buf[p - 1] != buf[p])) {
         int32_t end = p + 1;
         while (end < n && buf[end] == buf[p]) ++end;
-        q = (end - p) >= a.smin;
+        q = (end - p) >= smin;
       }
       cnt_total += __popc(__ballot_sync(0xffffffffu, q));
     }
@@ -145,7 +146,7 @@ __global__ __launch_bounds__(kWarpNT) void k_walk_warp(Walk w, const int32_t *__
           int32_t end = p + 1;
           while (end < n && buf[end] == buf[p]) ++end;
           c = end - p;
-          q = c >= a.smin;
+          q = c >= smin;
         }
         const unsigned bal = __ballot_sync(0xffffffffu, q);
         if (q) put(a, base, t0 + __popc(bal & ((1u << lane) - 1)), e, buf[p], c);
@@ -158,27 +159,34 @@ __global__ __launch_bounds__(kWarpNT) void k_walk_warp(Walk w, const int32_t *__
 
 // ------------------------------------------------- shared-memory tables --
 //
-// An open-addressing table of T = 2^lgT slots (keys = far ends f, cnts =
-// wedge counts) in shared memory, T >= 2 x (distinct keys) so it never fills.
-// After the walk, table_collect counts the slots with count >= s and, if
-// asked, packs them as (f << 32 | count) into the first entries of the keys
-// array (reused as a u64 buffer: at most T/2 entries) and sorts them by f.
+// An open-addressing table of T = 2^lgT 64-bit slots in shared memory, each
+// slot (f << 32 | count) for a far end f; kEmpty64 marks a free slot.  The
+// table holds at least twice the distinct keys it will receive, so it never
+// fills.  A new key costs one CAS, a repeated one a load and an add.  After
+// the walk, table_collect counts the slots with count >= s and, if asked,
+// moves them to the front of the table (they are already packed as sort keys)
+// and sorts them by f.
 
-__device__ __forceinline__ void table_insert(int32_t *keys, int32_t *cnts, int lgT, int32_t f,
+constexpr unsigned long long kEmpty64 = 0xFFFFFFFF00000000ull;
+
+__device__ __forceinline__ void table_insert(unsigned long long *tab, int lgT, int32_t f,
                                              int32_t add, int32_t smin, bool unweighted,
                                              Meta *meta) {
   const uint32_t mask = (1u << lgT) - 1u;
+  const unsigned long long key = (unsigned long long)(uint32_t)f << 32;
   uint32_t h = ((uint32_t)f * 0x9E3779B1u) >> (32 - lgT);
   for (uint32_t probe = 0; probe <= mask; ++probe) {
-    const int32_t k = *(volatile int32_t *)(keys + h);
-    if (k == f) {
-      if (!unweighted || *(volatile int32_t *)(cnts + h) < smin) atomicAdd(cnts + h, add);
+    const unsigned long long cur = *(volatile unsigned long long *)(tab + h);
+    if ((cur & kEmpty64) == key) {
+      if (!unweighted || (int32_t)(uint32_t)cur < smin) atomicAdd(tab + h, (unsigned long long)add);
       return;
     }
-    if (k == kEmpty) {
-      const int32_t prev = atomicCAS(keys + h, kEmpty, f);
-      if (prev == kEmpty || prev == f) {
-        atomicAdd(cnts + h, add);
+    if (cur == kEmpty64) {
+      const unsigned long long prev = atomicCAS(tab + h, kEmpty64, key | (uint32_t)add);
+      if (prev == kEmpty64) return;
+      if ((prev & kEmpty64) == key) {
+        if (!unweighted || (int32_t)(uint32_t)prev < smin)
+          atomicAdd(tab + h, (unsigned long long)add);
         return;
       }
     }
@@ -197,44 +205,49 @@ __device__ __forceinline__ int table_lg(int32_t distinct, int lg_max) {
   return lg < lg_max ? lg : lg_max;
 }
 
+// Rounds of RND slots per thread (slot = (round * RND + i) * NT + thread):
+// a round reads its slots into registers, a block scan places the ones that
+// qualify, and they are written to the front of the table.  A write of round
+// r lands below the number of qualifying slots seen so far, hence on a slot
+// of round r or earlier, all of which were read before the round's scan.
 template <int NT, int SPT>
-__device__ __forceinline__ int32_t table_collect(int32_t *keys, int32_t *cnts, int32_t T,
-                                                 int32_t smin, bool sort, int32_t *ws) {
-  int32_t kk[SPT], cc[SPT];
-  int32_t c = 0;
+__device__ __forceinline__ int32_t table_collect(unsigned long long *tab, int32_t T, int32_t smin,
+                                                 bool sort, int32_t *ws) {
+  constexpr int RND = SPT < 8 ? SPT : 8;
+  int32_t run = 0;
+  for (int32_t r0 = 0; r0 * NT < T; r0 += RND) {
+    unsigned long long kv[RND];
+    int32_t c = 0;
 #pragma unroll
-  for (int i = 0; i < SPT; ++i) {
-    const int32_t slot = i * NT + (int32_t)threadIdx.x;
-    kk[i] = kEmpty;
-    cc[i] = 0;
-    if (slot < T) {
-      kk[i] = keys[slot];
-      cc[i] = cnts[slot];
+    for (int i = 0; i < RND; ++i) {
+      const int32_t slot = (r0 + i) * NT + (int32_t)threadIdx.x;
+      kv[i] = slot < T ? tab[slot] : kEmpty64;
+      c += (kv[i] != kEmpty64) & ((int32_t)(uint32_t)kv[i] >= smin);
     }
-    c += (kk[i] != kEmpty) & (cc[i] >= smin);
-  }
-  int32_t total;
-  const int32_t inc = block_inclusive_scan<NT>(c, ws, &total);  // all slot reads done
-  if (sort && total > 0) {
-    unsigned long long *sb = reinterpret_cast<unsigned long long *>(keys);
-    int32_t pos = inc - c;
+    int32_t total;
+    const int32_t inc = block_inclusive_scan<NT>(c, ws, &total);  // the round's reads done
+    if (sort) {
+      int32_t pos = run + inc - c;
 #pragma unroll
-    for (int i = 0; i < SPT; ++i)
-      if (kk[i] != kEmpty && cc[i] >= smin)
-        sb[pos++] = ((unsigned long long)(uint32_t)kk[i] << 32) | (uint32_t)cc[i];
+      for (int i = 0; i < RND; ++i)
+        if (kv[i] != kEmpty64 && (int32_t)(uint32_t)kv[i] >= smin) tab[pos++] = kv[i];
+    }
+    run += total;
+  }
+  if (sort && run > 0) {
     int32_t n2 = 1;
-    while (n2 < total) n2 <<= 1;
-    for (int32_t i = total + threadIdx.x; i < n2; i += NT) sb[i] = ~0ull;
+    while (n2 < run) n2 <<= 1;
+    for (int32_t i = run + threadIdx.x; i < n2; i += NT) tab[i] = ~0ull;
     __syncthreads();
     for (int32_t k = 2; k <= n2; k <<= 1) {
       for (int32_t jj = k >> 1; jj > 0; jj >>= 1) {
         for (int32_t i = threadIdx.x; i < n2; i += NT) {
           const int32_t ixj = i ^ jj;
           if (ixj > i) {
-            const unsigned long long x = sb[i], y = sb[ixj];
+            const unsigned long long x = tab[i], y = tab[ixj];
             if ((x > y) == ((i & k) == 0)) {
-              sb[i] = y;
-              sb[ixj] = x;
+              tab[i] = y;
+              tab[ixj] = x;
             }
           }
         }
@@ -242,19 +255,16 @@ __device__ __forceinline__ int32_t table_collect(int32_t *keys, int32_t *cnts, i
       }
     }
   }
-  return total;
+  return run;
 }
 
 template <int NT, int SPT>
-__device__ __forceinline__ void table_reset(int32_t *keys, int32_t *cnts, int32_t T) {
-  __syncthreads();  // sorted entries may still be read from keys
+__device__ __forceinline__ void table_reset(unsigned long long *tab, int32_t T) {
+  __syncthreads();  // sorted entries may still be read
 #pragma unroll
   for (int i = 0; i < SPT; ++i) {
     const int32_t slot = i * NT + (int32_t)threadIdx.x;
-    if (slot < T) {
-      keys[slot] = kEmpty;
-      cnts[slot] = 0;
-    }
+    if (slot < T) tab[slot] = kEmpty64;
   }
   __syncthreads();
 }
@@ -264,14 +274,14 @@ __device__ __forceinline__ void table_reset(int32_t *keys, int32_t *cnts, int32_
 template <int NT, int TMAX>
 struct CtaCfg {
   static constexpr int kSPT = TMAX / NT;  // slots per thread at most
-  // [s_base 16 B][keys TMAX][cnts TMAX][s_beg NT][s_pref NT+1][ws NT/32+1]
+  // [s_base 16 B][table TMAX x 8 B][s_beg NT][s_pref NT+1][ws NT/32+1]
   static constexpr size_t smem() {
     return 16 + (size_t)TMAX * 8 + (size_t)(2 * NT + 1 + NT / 32 + 1) * 4;
   }
 };
 
-template <int NT, int TMAX, int BIN>
-__global__ __launch_bounds__(NT) void k_walk_cta(Walk w, const int32_t *__restrict__ rows,
+template <int NT, int TMAX, int BIN, int MINB>
+__global__ __launch_bounds__(NT, MINB) void k_walk_cta(Walk w, const int32_t *__restrict__ rows,
                                                  const int32_t *__restrict__ row_work,
                                                  EmitArgs a) {
   using Cfg = CtaCfg<NT, TMAX>;
@@ -279,98 +289,146 @@ __global__ __launch_bounds__(NT) void k_walk_cta(Walk w, const int32_t *__restri
   if (meta->err) return;
   extern __shared__ __align__(16) unsigned char smem[];
   long long *s_base = reinterpret_cast<long long *>(smem);
-  int32_t *keys = reinterpret_cast<int32_t *>(smem + 16);
-  int32_t *cnts = keys + TMAX;
-  int32_t *s_beg = cnts + TMAX;
+  unsigned long long *tab = reinterpret_cast<unsigned long long *>(smem + 16);
+  int32_t *s_beg = reinterpret_cast<int32_t *>(tab + TMAX);
   int32_t *s_pref = s_beg + NT;
   int32_t *ws = s_pref + NT + 1;
   constexpr int lg_max = (TMAX >= 2) ? 31 - __builtin_clz(TMAX) : 1;
 
-  for (int i = threadIdx.x; i < TMAX; i += NT) {
-    keys[i] = kEmpty;
-    cnts[i] = 0;
-  }
+  for (int i = threadIdx.x; i < TMAX; i += NT) tab[i] = kEmpty64;
   __syncthreads();
   const long long nrows = (long long)meta->rows_bin[BIN];
-  const int32_t smin = a.smin;
   const bool unweighted = a.unweighted != 0;
   const bool emit = a.mode != kCount;
   for (long long r = blockIdx.x; r < nrows; r += gridDim.x) {
     const int32_t e = rows[r];
+    const int32_t smin = s_of(a.row_s, a.smin, e);
     const int lgT = table_lg(row_work[e - a.row_begin], lg_max);
     const int32_t T = 1 << lgT;
-    cta_walk<NT, 4>(w, w.r_off[e], w.r_off[e + 1], s_beg, s_pref, ws, [&](int32_t f) {
-      table_insert(keys, cnts, lgT, f, 1, smin, unweighted, meta);
+    cta_walk<NT, 4>(w, w.r_off[e], w.r_off[e + 1], s_beg, s_pref, ws, [&](int32_t f, int32_t) {
+      table_insert(tab, lgT, f, 1, smin, unweighted, meta);
     });
-    const int32_t total = table_collect<NT, Cfg::kSPT>(keys, cnts, T, smin, emit, ws);
+    const int32_t total = table_collect<NT, Cfg::kSPT>(tab, T, smin, emit, ws);
     if (threadIdx.x == 0) *s_base = reserve(a, e, total, BIN);
     __syncthreads();
     const long long base = *s_base;
     if (emit && base >= 0) {
-      const unsigned long long *sb = reinterpret_cast<const unsigned long long *>(keys);
       for (int32_t i = threadIdx.x; i < total; i += NT) {
-        const unsigned long long x = sb[i];
+        const unsigned long long x = tab[i];
         put(a, base, i, e, (int32_t)(x >> 32), (int32_t)(uint32_t)x);
       }
     }
-    table_reset<NT, Cfg::kSPT>(keys, cnts, T);
+    table_reset<NT, Cfg::kSPT>(tab, T);
   }
 }
 
 // ------------------------------------------------------------- giant bin --
 //
-// A CTA takes one giant row at a time (dynamic ticket).  The row's far ends
-// f lie in [f_lo, R) (f_lo = e + 1 for the upper-triangle walk, 0 for whole
-// columns); they are split into NSB sub-ranges of 2^shift ids.
-//   1. walk, counting wedges per sub-range (shared histogram);
-//   2. exclusive scan; walk again, scattering every f into the CTA's global
-//      scratch grouped by sub-range (the scratch of the rows in flight stays
-//      in L2);
-//   3. consecutive sub-ranges are grouped into buckets of at most CAP wedges
-//      (a single larger sub-range forms its own bucket: it holds at most
-//      2^shift distinct ids); each bucket, in ascending f, is counted in the
-//      shared table, and its pairs (already in order) are appended to the
-//      row's output.
-// Nothing is counted in global memory and the output comes out sorted.
+// A CTA takes one giant row at a time (dynamic ticket); two CTAs share an
+// SM.  The row's far ends f lie in [f_lo, R) (f_lo = e + 1 for the
+// upper-triangle walk, 0 for whole columns).
+//   1. one load-balanced walk copies the row's far ends, in flattened wedge
+//      order, to the CTA's global scratch `flat` (coalesced stores);
+//   2. the id range is cut into super-chunks of at most kNSB sub-ranges of
+//      2^shift ids each (2^shift <= kGiantTMax / 4).  Per super-chunk: a pass
+//      over `flat` counts its wedges per sub-range (shared histogram), an
+//      exclusive scan, and a second pass scatters them to `wl`, grouped by
+//      sub-range;
+//   3. consecutive sub-ranges form buckets of at most CAP wedges (a single
+//      larger sub-range forms its own bucket: it holds at most 2^shift
+//      distinct ids); bucket by bucket, in ascending f, the shared table
+//      counts the far ends and the bucket's pairs (already in order) are
+//      appended to the row's output.
+// Core rows (tensor-core tile path) add their tile items (f, tile count) to
+// the buckets of their id ranges.  Nothing is counted in global memory and
+// the output comes out sorted.
 
-constexpr int kGiantNT = 1024;
-constexpr int kGiantTMax = 16384;
-constexpr int kNSB = 4096;  // sub-ranges per row
+// Geometry (compile-time; the defaults are the tuned values).
+#ifndef SLG_GIANT_NT
+#define SLG_GIANT_NT 512
+#endif
+#ifndef SLG_GIANT_TMAX
+#define SLG_GIANT_TMAX 8192
+#endif
+#ifndef SLG_GIANT_MINB
+#define SLG_GIANT_MINB 2
+#endif
+#ifndef SLG_DENSE_RATIO
+#define SLG_DENSE_RATIO 8  // a row is dense with >= 1 wedge per this many ids (swept: 8 best)
+#endif
+constexpr int kGiantNT = SLG_GIANT_NT;
+constexpr int kGiantTMax = SLG_GIANT_TMAX;
+constexpr int kNSBLog = 11;
+constexpr int kNSB = 1 << kNSBLog;  // sub-ranges per super-chunk
+constexpr int kShiftMax = 31 - __builtin_clz(kGiantTMax / 4);  // 2^shift <= kGiantTMax / 4
 constexpr int kGiantSPT = kGiantTMax / kGiantNT;
+constexpr int kDenseW = 2 * kGiantTMax;  // ids per dense window (int32 counters in the table)
 
-// [s_base 16][s_misc 16][keys TMAX][cnts TMAX][sub NSB][bstart NSB+1]
+// [s_base 16][s_misc 16][table TMAX x 8][sub NSB][subt NSB+1][bstart NSB+1]
 // [s_beg NT][s_pref NT+1][ws NT/32+1]
 constexpr size_t giant_smem() {
-  return 32 + (size_t)kGiantTMax * 8 + (size_t)(2 * kNSB + 1) * 4 +
+  return 32 + (size_t)kGiantTMax * 8 + (size_t)(3 * kNSB + 2) * 4 +
          (size_t)(2 * kGiantNT + 1 + kGiantNT / 32 + 1) * 4;
 }
 
-__global__ __launch_bounds__(kGiantNT) void k_walk_giant(Walk w, const int32_t *__restrict__ rows,
-                                                         EmitArgs a, int32_t *__restrict__ scratch,
-                                                         long long scratch_stride, int32_t R) {
+// Exclusive scan of the kNSB sub-range counters in place (P per thread);
+// returns the total.
+__device__ __forceinline__ int32_t scan_subranges(int32_t *a, int32_t *ws) {
+  constexpr int P = kNSB / kGiantNT;
+  int32_t v[P], t = 0;
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    v[q] = a[threadIdx.x * P + q];
+    t += v[q];
+  }
+  int32_t total;
+  const int32_t inc = block_inclusive_scan<kGiantNT>(t, ws, &total);
+  int32_t run = inc - t;
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    a[threadIdx.x * P + q] = run;
+    run += v[q];
+  }
+  __syncthreads();
+  return total;
+}
+
+// First position p in core_list[0, n) with core_list[p] >= x.
+__device__ __forceinline__ int32_t core_lower(const int32_t *core_list, int32_t n, int32_t x) {
+  int32_t a = 0, b = n;
+  while (a < b) {
+    const int32_t mid = (a + b) >> 1;
+    if (__ldg(core_list + mid) < x) a = mid + 1;
+    else b = mid;
+  }
+  return a;
+}
+
+__global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w, const int32_t *__restrict__ rows,
+                                                            EmitArgs a, int32_t *__restrict__ scratch,
+                                                            long long scratch_stride, int32_t R) {
   Meta *meta = a.meta;
   if (meta->err) return;
   extern __shared__ __align__(16) unsigned char smem[];
   long long *s_base = reinterpret_cast<long long *>(smem);
-  int32_t *s_misc = reinterpret_cast<int32_t *>(smem + 16);  // [0] row, [1] buckets
-  int32_t *keys = reinterpret_cast<int32_t *>(smem + 32);
-  int32_t *cnts = keys + kGiantTMax;
-  int32_t *sub = cnts + kGiantTMax;
-  int32_t *bstart = sub + kNSB;
+  int32_t *s_misc = reinterpret_cast<int32_t *>(smem + 16);  // [0] row, [1] buckets, [2,3] items
+  unsigned long long *tab = reinterpret_cast<unsigned long long *>(smem + 32);
+  int32_t *sub = reinterpret_cast<int32_t *>(tab + kGiantTMax);
+  int32_t *subt = sub + kNSB;  // tile items per sub-range (core rows)
+  int32_t *bstart = subt + kNSB + 1;
   int32_t *s_beg = bstart + kNSB + 1;
   int32_t *s_pref = s_beg + kGiantNT;
   int32_t *ws = s_pref + kGiantNT + 1;
-  // per-CTA global scratch: wedge ends, then the row's staged pairs (j, w)
-  int32_t *wl = scratch + (long long)blockIdx.x * scratch_stride;
-  int32_t *tj = wl + scratch_stride / 3;
-  int32_t *tw = tj + scratch_stride / 3;
+  // per-CTA global scratch, 4 ints per wedge of the largest row:
+  // flattened far ends, far ends grouped by sub-range, staged pairs (j, w)
+  const long long q4 = scratch_stride / 4;
+  int32_t *flat = scratch + (long long)blockIdx.x * scratch_stride;
+  int32_t *wl = flat + q4;
+  int32_t *tj = wl + q4;
+  int32_t *tw = tj + q4;
 
-  for (int i = threadIdx.x; i < kGiantTMax; i += kGiantNT) {
-    keys[i] = kEmpty;
-    cnts[i] = 0;
-  }
+  for (int i = threadIdx.x; i < kGiantTMax; i += kGiantNT) tab[i] = kEmpty64;
   const unsigned nrows = (unsigned)meta->rows_bin[kBinGiant];
-  const int32_t smin = a.smin;
   const bool unweighted = a.unweighted != 0;
   const bool emit = a.mode != kCount;
   constexpr int lg_max = 31 - __builtin_clz(kGiantTMax);
@@ -383,99 +441,213 @@ __global__ __launch_bounds__(kGiantNT) void k_walk_giant(Walk w, const int32_t *
     __syncthreads();
     const int32_t e = s_misc[0];
     if (e < 0) break;
-    // far ends lie in [f_lo, R): (e, R) for the upper-triangle walk, the
-    // whole [0, R) when the tails are whole columns
+    const int32_t smin = s_of(a.row_s, a.smin, e);
     const int32_t f_lo = a.full_rows ? 0 : e + 1;
     const int32_t span = R - f_lo;
-    const int shift = max(0, ceil_log2(span) - 12);  // kNSB = 2^12
-    const int32_t nsb = ((span - 1) >> shift) + 1;
+    const int shift = min(kShiftMax, max(0, ceil_log2(span) - kNSBLog));
+    const int32_t chunk_w = kNSB << shift;  // ids per super-chunk
     const int32_t cap = kGiantTMax / 2 - (1 << shift);
-    const int32_t k0 = w.r_off[e], k1 = w.r_off[e + 1];
-    // 1. histogram of sub-ranges
-    for (int i = threadIdx.x; i < kNSB; i += kGiantNT) sub[i] = 0;
-    __syncthreads();
-    cta_walk<kGiantNT, 4>(w, k0, k1, s_beg, s_pref, ws, [&](int32_t f) {
-      atomicAdd(sub + ((f - f_lo) >> shift), 1);
-    });
-    // 2. exclusive scan (4 sub-ranges per thread), then scatter
-    {
-      constexpr int P = kNSB / kGiantNT;
-      int32_t v[P], t = 0;
-#pragma unroll
-      for (int q = 0; q < P; ++q) {
-        v[q] = sub[threadIdx.x * P + q];
-        t += v[q];
-      }
-      int32_t total;
-      const int32_t inc = block_inclusive_scan<kGiantNT>(t, ws, &total);
-      int32_t run = inc - t;
-#pragma unroll
-      for (int q = 0; q < P; ++q) {
-        sub[threadIdx.x * P + q] = run;
-        run += v[q];
-      }
-      __syncthreads();
+    const int32_t work = a.row_work[e - a.row_begin];
+    // Dense rows (at least one wedge per 8 ids) count fixed windows of
+    // kDenseW ids in a dense shared array: no hashing, no sort.
+    const bool dense = (long long)work * SLG_DENSE_RATIO >= (long long)span;
+    if (work > q4) {  // the scratch is sized by the largest row: cannot happen
+      if (threadIdx.x == 0) raise_error(meta, SLG_ERR_INVALID, kWhereGiant);
+      break;
     }
-    cta_walk<kGiantNT, 4>(w, k0, k1, s_beg, s_pref, ws, [&](int32_t f) {
-      wl[atomicAdd(sub + ((f - f_lo) >> shift), 1)] = f;
-    });
-    // now sub[b] = end of sub-range b = start of b + 1
-    // 3. bucket starts: sub-range b opens a bucket when start(b) / cap changes
-    {
-      constexpr int P = kNSB / kGiantNT;
-      int32_t flag[P], t = 0;
-#pragma unroll
-      for (int q = 0; q < P; ++q) {
-        const int32_t b = threadIdx.x * P + q;
-        flag[q] = 0;
-        if (b < nsb) {
-          const int32_t st = b ? sub[b - 1] : 0;
-          const int32_t sp = b > 1 ? sub[b - 2] : 0;
-          flag[q] = (b == 0) || (st / cap != sp / cap);
-        }
-        t += flag[q];
-      }
-      int32_t total;
-      const int32_t inc = block_inclusive_scan<kGiantNT>(t, ws, &total);
-      int32_t pos = inc - t;
-#pragma unroll
-      for (int q = 0; q < P; ++q)
-        if (flag[q]) bstart[pos++] = threadIdx.x * P + q;
-      if (threadIdx.x == 0) {
-        bstart[total] = nsb;
-        s_misc[1] = total;
-      }
-      __syncthreads();
-    }
-    const int32_t nb = s_misc[1];
+    long long clk0 = clock64();
+    // 1. flattened far ends
+    cta_walk<kGiantNT, 4>(w, w.r_off[e], w.r_off[e + 1], s_beg, s_pref, ws,
+                          [&](int32_t f, int32_t i) { flat[i] = f; });
+    long long clk_part = 0, clk_bucket = 0;
+    if (threadIdx.x == 0) atomicAdd(&meta->giant_cycles[0], (unsigned long long)(clock64() - clk0));
+    // Core rows also receive tile items (f, |e ∩ f ∩ C_c|) for every active
+    // core row f > e with a non-zero tile count.
+    const CoreInfo &ci = a.core;
+    const bool core_row = ci.T && ci.row_rank[e + 1] != ci.row_rank[e];
+    const int32_t ri = core_row ? ci.row_rank[e] : 0;
+    const int32_t *Trow = core_row ? ci.T + (long long)ri * ci.Mp : nullptr;
     long long base = -1;
     if (a.mode == kDirect) base = a.row_ptr[e - a.row_begin];
     int32_t out = 0;  // pairs of the row so far
-    for (int32_t c = 0; c < nb; ++c) {
-      const int32_t b0 = bstart[c], b1 = bstart[c + 1];
-      const int32_t lo = b0 ? sub[b0 - 1] : 0, hi = sub[b1 - 1];
-      const int32_t width = (b1 - b0) << shift;
-      const int lgT = table_lg(min(hi - lo, width), lg_max);
-      const int32_t T = 1 << lgT;
-      for (int32_t i = lo + (int32_t)threadIdx.x; i < hi; i += kGiantNT)
-        table_insert(keys, cnts, lgT, wl[i], 1, smin, unweighted, meta);
+    for (int32_t F0 = f_lo; F0 < R; F0 += chunk_w) {
+      const long long c0 = clock64();
+      const int32_t F1 = (R - F0 > chunk_w) ? F0 + chunk_w : R;
+      const int32_t nsb = ((F1 - F0 - 1) >> shift) + 1;
+      // 2. histograms of sub-ranges (wedges; tile items), scans, scatter
+      for (int i = threadIdx.x; i < kNSB; i += kGiantNT) {
+        sub[i] = 0;
+        subt[i] = 0;
+      }
       __syncthreads();
-      const int32_t total = table_collect<kGiantNT, kGiantSPT>(keys, cnts, T, smin, emit, ws);
-      if (emit && total > 0) {
-        const unsigned long long *sb = reinterpret_cast<const unsigned long long *>(keys);
-        for (int32_t i = threadIdx.x; i < total; i += kGiantNT) {
-          const unsigned long long x = sb[i];
-          const int32_t f = (int32_t)(x >> 32), n = (int32_t)(uint32_t)x;
-          if (a.mode == kDirect) {
-            put(a, base, out + i, e, f, n);
-          } else {
-            tj[out + i] = f;
-            if (!unweighted) tw[out + i] = n;
+      for (int32_t i = threadIdx.x; i < work; i += kGiantNT) {
+        const int32_t f = flat[i];
+        if (f >= F0 && f < F1) atomicAdd(sub + ((f - F0) >> shift), 1);
+      }
+      if (core_row)
+        for (int32_t p = ri + 1 + (int32_t)threadIdx.x; p < ci.n_core; p += kGiantNT) {
+          const int32_t f = ci.core_list[p];
+          if (f >= F0 && f < F1 && w.r_off[f + 1] - w.r_off[f] >= smin && Trow[p] > 0)
+            atomicAdd(subt + ((f - F0) >> shift), 1);
+        }
+      __syncthreads();
+      const int32_t nw = scan_subranges(sub, ws);
+      const int32_t items = core_row ? scan_subranges(subt, ws) : 0;
+      if (nw == 0 && items == 0) continue;  // uniform: both totals are block-wide
+      if (threadIdx.x == 0) subt[kNSB] = items;
+      for (int32_t i = threadIdx.x; i < work; i += kGiantNT) {
+        const int32_t f = flat[i];
+        if (f >= F0 && f < F1) wl[atomicAdd(sub + ((f - F0) >> shift), 1)] = f;
+      }
+      __syncthreads();
+      // now sub[b] = end of the wedges of sub-range b; subt[b] = start of its
+      // items.  3. bucket starts: sub-range b opens a bucket when its start
+      // in the merged order (wedges + items before it) / cap changes.
+      {
+        constexpr int P = kNSB / kGiantNT;
+        int32_t flag[P], t = 0;
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+          const int32_t b = threadIdx.x * P + q;
+          flag[q] = 0;
+          if (b < nsb) {
+            if (dense) {
+              flag[q] = ((b << shift) & (kDenseW - 1)) == 0;
+            } else {
+              const int32_t st = (b ? sub[b - 1] : 0) + (core_row ? subt[b] : 0);
+              const int32_t sp = b ? (b > 1 ? sub[b - 2] : 0) + (core_row ? subt[b - 1] : 0) : 0;
+              flag[q] = (b == 0) || (st / cap != sp / cap);
+            }
+          }
+          t += flag[q];
+        }
+        int32_t total;
+        const int32_t inc = block_inclusive_scan<kGiantNT>(t, ws, &total);
+        int32_t pos = inc - t;
+#pragma unroll
+        for (int q = 0; q < P; ++q)
+          if (flag[q]) bstart[pos++] = threadIdx.x * P + q;
+        if (threadIdx.x == 0) {
+          bstart[total] = nsb;
+          s_misc[1] = total;
+        }
+        __syncthreads();
+      }
+      const int32_t nb = s_misc[1];
+      const long long c1 = clock64();
+      clk_part += c1 - c0;
+      for (int32_t c = 0; c < nb; ++c) {
+        const int32_t b0 = bstart[c], b1 = bstart[c + 1];
+        const int32_t lo = b0 ? sub[b0 - 1] : 0, hi = sub[b1 - 1];
+        int32_t nit = 0;
+        if (core_row) {
+          nit = (b1 < nsb ? subt[b1] : subt[kNSB]) - subt[b0];
+          if (threadIdx.x == 0) {
+            // core positions of the bucket's id range, after row e itself
+            const int32_t flo = F0 + (b0 << shift);
+            const int32_t fhi = b1 < nsb ? F0 + (b1 << shift) : F1;
+            s_misc[2] = max(core_lower(ci.core_list, ci.n_core, flo), ri + 1);
+            s_misc[3] = core_lower(ci.core_list, ci.n_core, fhi);
+          }
+          __syncthreads();
+        }
+        if (hi - lo + nit == 0) continue;  // uniform
+        if (dense) {
+          const int32_t fb0 = F0 + (b0 << shift);
+          const int32_t dw = min((b1 - b0) << shift, F1 - fb0);  // <= kDenseW
+          int32_t *cnt = reinterpret_cast<int32_t *>(tab);
+          for (int32_t i = threadIdx.x; i < dw; i += kGiantNT) cnt[i] = 0;
+          __syncthreads();
+          for (int32_t i = lo + (int32_t)threadIdx.x; i < hi; i += kGiantNT)
+            atomicAdd(cnt + (wl[i] - fb0), 1);
+          if (core_row && nit > 0)
+            for (int32_t p = s_misc[2] + (int32_t)threadIdx.x; p < s_misc[3]; p += kGiantNT) {
+              const int32_t f = ci.core_list[p];
+              const int32_t wt = Trow[p];
+              if (wt > 0 && w.r_off[f + 1] - w.r_off[f] >= smin) atomicAdd(cnt + (f - fb0), wt);
+            }
+          __syncthreads();
+          // ordered emission: warp q owns counters [q * span_w, (q + 1) * span_w)
+          const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+          constexpr int NWq = kGiantNT / 32;
+          const int32_t span_w = ((dw + NWq - 1) / NWq + 31) & ~31;
+          const int32_t q0 = wq * span_w, q1 = min(dw, q0 + span_w);
+          int32_t c = 0;
+          for (int32_t i = q0 + lane; i < q1; i += 32) c += cnt[i] >= smin;
+#pragma unroll
+          for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+          int32_t total;
+          const int32_t winc = block_inclusive_scan<kGiantNT>(lane == 0 ? c : 0, ws, &total);
+          int32_t pos = out + __shfl_sync(0xffffffffu, winc, 0) - c;  // warp's first slot
+          if (a.mode == kStage && out + total > q4) {
+            if (threadIdx.x == 0) raise_error(meta, SLG_ERR_INVALID, kWhereGiant);
+            break;
+          }
+          if (emit && total > 0) {
+            for (int32_t i0 = q0; i0 < q1; i0 += 32) {
+              const int32_t i = i0 + lane;
+              const int32_t n = i < q1 ? cnt[i] : 0;
+              const bool keep = i < q1 && n >= smin;
+              const unsigned bal = __ballot_sync(0xffffffffu, keep);
+              if (keep) {
+                const int32_t t = pos + __popc(bal & ((1u << lane) - 1));
+                if (a.mode == kDirect) {
+                  put(a, base, t, e, fb0 + i, n);
+                } else {
+                  tj[t] = fb0 + i;
+                  if (!unweighted) tw[t] = n;
+                }
+              }
+              pos += __popc(bal);
+            }
+          }
+          out += total;
+          __syncthreads();
+          for (int32_t i = threadIdx.x; i < (dw + 1) / 2; i += kGiantNT) tab[i] = kEmpty64;
+          __syncthreads();
+          continue;
+        }
+        const int32_t width = (b1 - b0) << shift;
+        const int lgT = table_lg(min(hi - lo + nit, width), lg_max);
+        const int32_t T = 1 << lgT;
+        for (int32_t i = lo + (int32_t)threadIdx.x; i < hi; i += kGiantNT)
+          table_insert(tab, lgT, wl[i], 1, smin, unweighted, meta);
+        if (core_row && nit > 0)
+          for (int32_t p = s_misc[2] + (int32_t)threadIdx.x; p < s_misc[3]; p += kGiantNT) {
+            const int32_t f = ci.core_list[p];
+            const int32_t wt = Trow[p];
+            if (wt > 0 && w.r_off[f + 1] - w.r_off[f] >= smin)
+              table_insert(tab, lgT, f, wt, smin, unweighted, meta);
+          }
+        __syncthreads();
+        const int32_t total = table_collect<kGiantNT, kGiantSPT>(tab, T, smin, emit, ws);
+        if (a.mode == kStage && out + total > q4) {
+          // staged pairs would not fit the scratch (sized by wedges + core
+          // items): report instead of writing past it
+          if (threadIdx.x == 0) raise_error(meta, SLG_ERR_INVALID, kWhereGiant);
+          table_reset<kGiantNT, kGiantSPT>(tab, T);
+          break;
+        }
+        if (emit && total > 0) {
+          for (int32_t i = threadIdx.x; i < total; i += kGiantNT) {
+            const unsigned long long x = tab[i];
+            const int32_t f = (int32_t)(x >> 32), n = (int32_t)(uint32_t)x;
+            if (a.mode == kDirect) {
+              put(a, base, out + i, e, f, n);
+            } else {
+              tj[out + i] = f;
+              if (!unweighted) tw[out + i] = n;
+            }
           }
         }
+        out += total;
+        table_reset<kGiantNT, kGiantSPT>(tab, T);
       }
-      out += total;
-      table_reset<kGiantNT, kGiantSPT>(keys, cnts, T);
+      clk_bucket += clock64() - c1;
+    }
+    if (threadIdx.x == 0) {
+      atomicAdd(&meta->giant_cycles[1], (unsigned long long)clk_part);
+      atomicAdd(&meta->giant_cycles[2], (unsigned long long)clk_bucket);
     }
     if (threadIdx.x == 0) *s_base = reserve(a, e, out, kBinGiant);
     __syncthreads();
@@ -495,9 +667,9 @@ __global__ __launch_bounds__(kGiantNT) void k_walk_giant(Walk w, const int32_t *
 namespace {
 
 using CfgS = CtaCfg<256, 2 * kCtaSMaxWork>;
-using CfgL = CtaCfg<1024, 2 * kCtaLMaxWork>;
-#define K_CTA_S k_walk_cta<256, 2 * kCtaSMaxWork, kBinCtaS>
-#define K_CTA_L k_walk_cta<1024, 2 * kCtaLMaxWork, kBinCtaL>
+using CfgL = CtaCfg<256, 2 * kCtaLMaxWork>;
+#define K_CTA_S k_walk_cta<256, 2 * kCtaSMaxWork, kBinCtaS, 4>
+#define K_CTA_L k_walk_cta<256, 2 * kCtaLMaxWork, kBinCtaL, 3>
 
 struct Occ {
   int sms = 0, warp_blocks = 0, s_blocks = 0, l_blocks = 0, g_blocks = 0;
@@ -506,9 +678,11 @@ struct Occ {
 
 Occ &occ_for_device() {
   static Occ occ[64];
+  static std::mutex mu;
   int dev = 0;
   cudaGetDevice(&dev);
   Occ &o = occ[dev & 63];
+  std::lock_guard<std::mutex> lock(mu);
   if (o.dev != dev) {
     cudaDeviceGetAttribute(&o.sms, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(K_CTA_S, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CfgS::smem());
@@ -517,7 +691,7 @@ Occ &occ_for_device() {
                          (int)giant_smem());
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.warp_blocks, k_walk_warp, kWarpNT, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.s_blocks, K_CTA_S, 256, CfgS::smem());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.l_blocks, K_CTA_L, 1024, CfgL::smem());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.l_blocks, K_CTA_L, 256, CfgL::smem());
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.g_blocks, k_walk_giant, kGiantNT,
                                                   giant_smem());
     if (o.g_blocks < 1) o.g_blocks = 1;
@@ -550,7 +724,7 @@ cudaError_t launch_walk(const WalkLaunch &L, cudaStream_t st, int32_t *launches,
       L.w, lists + 1 * stride, L.row_work, L.a);
   ++n;
   if (ev) cudaEventRecord(ev[2], st);
-  K_CTA_L<<<o.sms * (o.l_blocks > 0 ? o.l_blocks : 1), 1024, CfgL::smem(), st>>>(
+  K_CTA_L<<<o.sms * (o.l_blocks > 0 ? o.l_blocks : 1), 256, CfgL::smem(), st>>>(
       L.w, lists + 2 * stride, L.row_work, L.a);
   ++n;
   if (ev) cudaEventRecord(ev[3], st);

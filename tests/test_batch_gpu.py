@@ -1,0 +1,68 @@
+"""Batched form: many hypergraphs with their own s in one captured pipeline
+give, member by member, exactly the oracle's L_s."""
+import numpy as np
+import pytest
+
+import hypergen as hg
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+slg = pytest.importorskip("paper_2010_11448_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2010_11448_gb300 import build_lib
+    build_lib.build()
+    slg.load()
+
+
+def members(count, seed):
+    rng = np.random.default_rng(seed)
+    ms = np.exp(rng.uniform(np.log(200), np.log(8000), size=count)).astype(int)
+    ss = rng.integers(1, 12, size=count)
+    gs = [hg.chung_lu(int(m), 2 * int(m), seed=seed + k, size_cap=800)
+          for k, m in enumerate(ms)]
+    # a member without incidences and a member with a huge s
+    gs.append(hg.from_rows([[], []], 3))
+    ss = np.append(ss, 2)
+    gs.append(hg.uniform(300, 400, 1, 10, seed=5))
+    ss = np.append(ss, 1000)
+    return gs, [int(x) for x in ss]
+
+
+def as_np(t):
+    i, j, w = t
+    if i.shape[0] == 0:
+        return np.zeros((0, 3), np.int64)
+    return np.stack([i.cpu().numpy(), j.cpu().numpy(), w.cpu().numpy()], 1).astype(np.int64)
+
+
+@pytest.mark.parametrize("dual", [False, True])
+def test_members_match_oracle(dual):
+    gs, ss = members(24, 11)
+    plan = slg.Plan([slg.to_device(g) for g in gs], ss, dual=dual)
+    info = plan.info()
+    assert info["launches"] > 0 and info["tuned_ms"] > 0
+    assert info["bins"][0] <= 128 and info["bins"][1] <= 1024 and info["bins"][2] <= 4096
+    for rep in range(2):                     # the captured graph replays cleanly
+        plan.execute()
+        res = plan.results()
+        for g, s, r in zip(gs, ss, res):
+            want = oracle.canonical(*oracle.line_graph_of(g, s, dual=dual, threads=4))
+            assert np.array_equal(as_np(r), want)
+    plan.close()
+
+
+def test_unweighted_batch_pairs():
+    gs, ss = members(8, 3)
+    plan = slg.Plan([slg.to_device(g) for g in gs], ss, unweighted=True)
+    plan.execute()
+    for g, s, (i, j, w) in zip(gs, ss, plan.results()):
+        assert w is None
+        want = oracle.canonical(*oracle.line_graph_of(g, s))
+        got = np.stack([i.cpu().numpy(), j.cpu().numpy()], 1) if i.shape[0] else np.zeros((0, 2))
+        assert np.array_equal(got, want[:, :2])
