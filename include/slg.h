@@ -69,7 +69,9 @@ typedef enum slg_status {
   SLG_ERR_NOMEM = 3,       /* device allocation failed */
   SLG_ERR_CUDA = 4,        /* a CUDA runtime call failed */
   SLG_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
-  SLG_ERR_UNSUPPORTED = 6  /* flag combination not provided */
+  SLG_ERR_UNSUPPORTED = 6, /* flag combination not provided */
+  SLG_ERR_TOO_LARGE = 7    /* input larger than slg_count_noalloc's fixed
+                              working memory */
 } slg_status;
 
 /* Flags (bitwise OR). */
@@ -211,6 +213,41 @@ int slg_plan_result(const slg_plan *plan, const int32_t **out_i,
 int slg_plan_info(const slg_plan *plan, int32_t *bins, float *tuned_ms,
                   int32_t *launches);
 int slg_plan_destroy(slg_plan *plan);
+
+/*
+ * slg_count_noalloc -- the same count as slg_count, for callers that must
+ * not allocate device memory during the call.
+ *
+ * Who needs it: some callers cannot call cudaMalloc at the time they need
+ * the count.  A process whose device memory is already claimed by another
+ * allocator (for example a framework's caching allocator that reserves
+ * nearly the whole GPU up front) would see the allocation fail.  A
+ * latency-bound loop cannot afford an allocation that waits behind work
+ * already queued on the device.  This entry point allocates nothing.  Its
+ * working memory is one fixed 64 MiB device array built into the library,
+ * which every GPU that loads the library keeps until the process exits.
+ * The paper has no counterpart; this is a library convenience.
+ *
+ *   h, s, n_pairs, stream  as for slg_count
+ *   flags                  SLG_DUAL and SLG_UNWEIGHTED only
+ *
+ * Limits and behaviour:
+ *  - Size: the computed side may have at most 2,094,080 rows (hyperedges of
+ *    H, or vertices with SLG_DUAL).  Larger inputs return SLG_ERR_TOO_LARGE
+ *    without any device work.
+ *  - The first call on a device looks up the array's device address (once
+ *    per device); make that first call before any stream capture.
+ *  - Every call shares the array and keeps the previous call's contents;
+ *    each call clears the part it uses at its start.  Calls whose work
+ *    overlaps on the GPU (other streams, other host threads) race on the
+ *    array: do not let them overlap.
+ *  - The input is checked on the device (offsets, id ranges, ascending
+ *    rows) but, unlike slg_count, not cross-checked between CSR and CSC.
+ *  - It runs the plain per-hyperedge kernel (one warp per hyperedge), so it
+ *    is slower than slg_count.
+ */
+int slg_count_noalloc(const slg_hypergraph *h, int32_t s, uint32_t flags,
+                      int64_t *n_pairs, void *stream);
 
 /* Statistics of the last call made by this host thread.  Bins: 0 = warp
  * (small rows), 1 = CTA small, 2 = CTA large, 3 = giant rows. */

@@ -85,6 +85,7 @@ _HP = ctypes.POINTER(_Hypergraph)
 # name -> (restype, argtypes); every symbol include/slg.h declares.
 ABI_FUNCTIONS = {
     "slg_count": (ctypes.c_int, [_HP, ctypes.c_int32, ctypes.c_uint32, _I64P, _VP]),
+    "slg_count_noalloc": (ctypes.c_int, [_HP, ctypes.c_int32, ctypes.c_uint32, _I64P, _VP]),
     "slg_build": (ctypes.c_int, [_HP, ctypes.c_int32, ctypes.c_uint32, _VP, _VP, _VP,
                                  ctypes.c_int64, _I64P, _VP]),
     "slg_build_rows": (ctypes.c_int, [_HP, ctypes.c_int32, ctypes.c_uint32,

@@ -905,6 +905,7 @@ const char *slg_strerror(int status) {
     case SLG_ERR_CUDA: return "CUDA runtime error";
     case SLG_ERR_TIMEOUT: return "bounded device wait gave up";
     case SLG_ERR_UNSUPPORTED: return "unsupported flag combination or size";
+    case SLG_ERR_TOO_LARGE: return "input too large for the fixed working memory of slg_count_noalloc";
     default: return "unknown status";
   }
 }
