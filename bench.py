@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--algo", choices=["binned", "plain", "spgemm"], default="binned")
+    ap.add_argument("--relabel", choices=["none", "asc", "desc"], default="none",
+                    help="degree-ordered relabelling of the rows before the walk")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (testing)")
@@ -298,6 +300,7 @@ def run_ours(args):
     h = make_workload(rank, args.scale)
     dh = slg.to_device(h, dev)
     algo = args.algo
+    rl = None if args.relabel == "none" else args.relabel
     J = jobs()
     caps, wedges = {}, {}
     for dual, s in J:
@@ -312,7 +315,7 @@ def run_ours(args):
 
     def step(record):
         for dual, s in J:
-            slg.build(dh, s, dual=dual, algo=algo, out=outs[(dual, s)])
+            slg.build(dh, s, dual=dual, algo=algo, out=outs[(dual, s)], relabel=rl)
             if record:
                 st = slg.last_stats()
                 stats_acc["launches"] += st["kernel_launches"]
@@ -321,7 +324,8 @@ def run_ours(args):
                         stats_acc["ms_walk"][b] += st["ms_walk"][b]
                         stats_acc["bytes_walk"][b] += walk_bytes(st, b)
                         stats_acc["launch_walk"][b] += 1
-                    stats_acc["ms_other"] += st["ms_plan"] + st["ms_scan"] + st["ms_gather"]
+                    stats_acc["ms_other"] += (st["ms_plan"] + st["ms_scan"] + st["ms_gather"] +
+                                              st["ms_relabel"] + st["ms_order"])
 
     for _ in range(max(args.warmup, 0)):
         step(False)
@@ -370,6 +374,7 @@ def run_ours(args):
               "dtype": "int32", "data": "synthetic",
               "config": {"workload": WORKLOAD_TEXT, "m": h.m, "n": h.n, "nnz": h.nnz,
                          "s": list(S_VALUES), "sides": ["H", "H*"], "algo": algo,
+                         "relabel": args.relabel,
                          "wedges_per_step": W_step, "pairs_per_step": P_step,
                          "l2": "inputs (CSR+CSC 168 MB) larger than the 129 MB L2; no flush",
                          "parallelism": f"independent instance per rank x{world}"},
@@ -381,7 +386,7 @@ def run_ours(args):
     for dual, s in J:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        slg.build(dh, s, dual=dual, algo=algo, out=outs[(dual, s)])
+        slg.build(dh, s, dual=dual, algo=algo, out=outs[(dual, s)], relabel=rl)
         per[f"{'H*' if dual else 'H'} s={s}"] = (time.perf_counter() - t0) * 1e3
     result["build_ms"] = per
 
@@ -400,7 +405,7 @@ def run_ours(args):
 
         def e2e_step():
             for dual, s in J:
-                slg.build_host(hh, s, dual=dual, algo=algo, out=houts[(dual, s)])
+                slg.build_host(hh, s, dual=dual, algo=algo, out=houts[(dual, s)], relabel=rl)
         e2e_step()
         torch.cuda.synchronize()
         k2 = max(1, min(args.steps, 3))

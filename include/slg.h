@@ -86,6 +86,17 @@ typedef enum slg_status {
                                 wedges and the tile counts are added before
                                 the threshold, so the result is unchanged.
                                 Binned algorithm only. */
+#define SLG_RELABEL_ASC 0x8u  /* renumber the rows of the computed side by
+                                ascending size before the walk (the
+                                degree-ordered relabelling of Section IV-F),
+                                then map the pairs back and restore the
+                                canonical (i, j) order: the result is
+                                unchanged, only which row carries each pair's
+                                work differs.  Whole-side calls only (not
+                                slg_build_rows, not plans); needs |L_s| <
+                                2^31 for slg_build. */
+#define SLG_RELABEL_DESC 0x10u /* the same by descending size; at most one
+                                  of the two relabel flags */
 /* Algorithm selector (mutually exclusive values in bits 8..11). */
 #define SLG_ALGO_MASK 0xF00u
 #define SLG_ALGO_BINNED 0x000u /* default: degree-binned wedge walk */
@@ -100,7 +111,8 @@ typedef enum slg_status {
  * slg_count -- number of pairs of L_s (Section III) without writing them.
  *   h        incidence of H (device arrays as described above)
  *   s        overlap threshold, s >= 1 (s larger than every hyperedge gives 0)
- *   flags    SLG_DUAL, SLG_UNWEIGHTED, one SLG_ALGO_* value
+ *   flags    SLG_DUAL, SLG_UNWEIGHTED, SLG_TENSOR_CORE, SLG_RELABEL_ASC or
+ *            SLG_RELABEL_DESC, one SLG_ALGO_* value
  *   n_pairs  host pointer, receives |L_s|
  *   stream   cudaStream_t to run on
  * Returns SLG_OK, SLG_ERR_INVALID (s < 1, NULL pointers, negative sizes,
@@ -191,7 +203,7 @@ int slg_tile_overlap(const uint8_t *A, int32_t rows_pad, int32_t cols_pad,
  *     flags  SLG_DUAL, SLG_UNWEIGHTED
  *     plan   receives the plan (free with slg_plan_destroy)
  *   Synchronises `stream`.  Errors as for slg_build; SLG_ERR_UNSUPPORTED for
- *   SLG_TENSOR_CORE or an algorithm flag.
+ *   SLG_TENSOR_CORE, SLG_RELABEL_* or an algorithm flag.
  * slg_plan_execute -- replays the captured build on `stream`: one graph
  *   launch, no host synchronisation, results valid when the stream reaches
  *   that point.
@@ -271,15 +283,19 @@ typedef struct slg_stats {
   int64_t giant_cycles[3]; /* giant bin, SM clock cycles summed over CTAs:
                               walk, partition into buckets, bucket counting */
   int64_t max_row_work;    /* largest wedge count of one row */
+  float ms_relabel;        /* SLG_RELABEL_*: building the renumbered side */
+  float ms_order;          /* SLG_RELABEL_*: caller ids and (i, j) order */
 } slg_stats;
 
 int slg_last_stats(slg_stats *out);
 
 /*
  * slg_set_core_params -- dense-core selection for SLG_TENSOR_CORE on later
- * calls from this host thread: core columns have degree >= tau_c, core rows
- * have >= tau_r incidences in core columns, and the block is used when it
- * has at least 128 rows, 32 columns and a density >= min_density.
+ * calls from this host thread: candidate columns have degree >= tau_c and
+ * candidate rows >= tau_r incidences in them; the columns are then re-taken
+ * as those holding at least max(8, min_density x |rows|) candidate rows, and
+ * the rows again against those columns.  The block is used when it has at
+ * least 128 rows, 32 columns and a density >= min_density.
  * Defaults: 64, 32, 0.02.  Returns SLG_ERR_INVALID for values < 1 or a
  * density outside (0, 1].
  */

@@ -21,7 +21,8 @@ import numpy as np
 __all__ = [
     "DeviceHypergraph", "to_device", "count", "build", "build_rows",
     "build_host", "wedges", "last_stats", "set_profiling", "tile_overlap",
-    "set_core_params", "SLG_TENSOR_CORE", "Plan", "alloc_outputs",
+    "set_core_params", "SLG_TENSOR_CORE", "SLG_RELABEL_ASC", "SLG_RELABEL_DESC",
+    "Plan", "alloc_outputs",
     "library_path", "load",
     "SLG_DUAL", "SLG_UNWEIGHTED", "SLG_ALGO_BINNED", "SLG_ALGO_PLAIN",
     "SLG_ALGO_SPGEMM", "SlgError", "ABI_FUNCTIONS",
@@ -30,11 +31,14 @@ __all__ = [
 SLG_DUAL = 0x1
 SLG_UNWEIGHTED = 0x2
 SLG_TENSOR_CORE = 0x4
+SLG_RELABEL_ASC = 0x8
+SLG_RELABEL_DESC = 0x10
 SLG_ALGO_BINNED = 0x000
 SLG_ALGO_PLAIN = 0x100
 SLG_ALGO_SPGEMM = 0x200
 _ALGOS = {"binned": SLG_ALGO_BINNED, "plain": SLG_ALGO_PLAIN,
           "spgemm": SLG_ALGO_SPGEMM}
+_RELABEL = {None: 0, "asc": SLG_RELABEL_ASC, "desc": SLG_RELABEL_DESC}
 
 SLG_ERR_CAPACITY = 2
 
@@ -75,7 +79,9 @@ class _Stats(ctypes.Structure):
                 ("core_cols", ctypes.c_int64),
                 ("core_nnz", ctypes.c_int64),
                 ("giant_cycles", ctypes.c_int64 * 3),
-                ("max_row_work", ctypes.c_int64)]
+                ("max_row_work", ctypes.c_int64),
+                ("ms_relabel", ctypes.c_float),
+                ("ms_order", ctypes.c_float)]
 
 
 _I64P = ctypes.POINTER(ctypes.c_int64)
@@ -176,8 +182,8 @@ def to_device(h, device="cuda") -> DeviceHypergraph:
     return DeviceHypergraph(h.m, h.n, t(h.e_off), t(h.e_idx), t(h.v_off), t(h.v_idx))
 
 
-def _flags(dual, unweighted, algo, tensor=False):
-    f = _ALGOS[algo]
+def _flags(dual, unweighted, algo, tensor=False, relabel=None):
+    f = _ALGOS[algo] | _RELABEL[relabel]
     if tensor:
         f |= SLG_TENSOR_CORE
     if dual:
@@ -195,11 +201,11 @@ def _stream(stream):
 
 
 def count(h: DeviceHypergraph, s: int, dual=False, unweighted=False,
-          algo="binned", stream=None, tensor=False) -> int:
+          algo="binned", stream=None, tensor=False, relabel=None) -> int:
     """|L_s(H)| (or of H* with dual=True)."""
     n = ctypes.c_int64(0)
     rc = load().slg_count(ctypes.byref(h.struct), int(s),
-                          _flags(dual, unweighted, algo, tensor),
+                          _flags(dual, unweighted, algo, tensor, relabel),
                           ctypes.byref(n), _stream(stream))
     if rc != 0:
         raise SlgError(rc, "slg_count")
@@ -221,12 +227,14 @@ def _outputs(capacity, unweighted, device):
 
 
 def build(h: DeviceHypergraph, s: int, dual=False, unweighted=False,
-          algo="binned", capacity=None, out=None, stream=None, tensor=False):
+          algo="binned", capacity=None, out=None, stream=None, tensor=False,
+          relabel=None):
     """The canonical edge list of L_s as int32 tensors (i, j, w); w is None
     with unweighted=True.  Without ``capacity``/``out`` the pair count is
     taken first with ``count`` (an extra walk).  tensor=True counts a dense
-    core block on the tensor cores (same result)."""
-    flags = _flags(dual, unweighted, algo, tensor)
+    core block on the tensor cores; relabel="asc"/"desc" renumbers the rows
+    by size for the walk (both give the same result)."""
+    flags = _flags(dual, unweighted, algo, tensor, relabel)
     if out is None:
         if capacity is None:
             capacity = count(h, s, dual, unweighted, algo, stream, tensor)
@@ -268,7 +276,7 @@ def build_rows(h: DeviceHypergraph, s: int, row_begin: int, row_end: int,
 
 
 def build_host(h, s: int, dual=False, unweighted=False, algo="binned",
-               capacity: int = 0, out=None, stream=None):
+               capacity: int = 0, out=None, stream=None, relabel=None):
     """End-to-end from host arrays: ``h`` holds numpy (ideally pinned torch
     CPU) int32 arrays; the library copies them in, builds, copies back.
     ``out`` = three host int32 arrays of the same capacity."""
@@ -284,7 +292,8 @@ def build_host(h, s: int, dual=False, unweighted=False, algo="binned",
                None if unweighted else np.empty(cap, np.int32))
     oi, oj, ow = out
     n = ctypes.c_int64(0)
-    rc = load().slg_build_host(ctypes.byref(st), int(s), _flags(dual, unweighted, algo),
+    rc = load().slg_build_host(ctypes.byref(st), int(s),
+                               _flags(dual, unweighted, algo, relabel=relabel),
                                ptr(oi), ptr(oj), ptr(ow) if ow is not None else None,
                                int(oi.shape[0]), ctypes.byref(n), _stream(stream))
     if rc != 0:
@@ -315,7 +324,8 @@ def last_stats() -> dict:
             "ms_plan": st.ms_plan, "ms_walk": list(st.ms_walk), "ms_scan": st.ms_scan,
             "ms_gather": st.ms_gather, "core_rows": st.core_rows, "core_cols": st.core_cols,
             "core_nnz": st.core_nnz, "giant_cycles": list(st.giant_cycles),
-            "max_row_work": st.max_row_work}
+            "max_row_work": st.max_row_work, "ms_relabel": st.ms_relabel,
+            "ms_order": st.ms_order}
 
 
 def set_core_params(tau_c: int = 64, tau_r: int = 32, min_density: float = 0.02) -> None:

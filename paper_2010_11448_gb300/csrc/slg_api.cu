@@ -2,6 +2,7 @@
 // per-call working memory, the sequence of planning, walking and output
 // kernels, and the single device->host read of the pair count.
 #include <algorithm>
+#include <cmath>
 #include <memory>
 #include <mutex>
 #include <vector>
@@ -30,9 +31,9 @@ thread_local Bins t_bins;
 thread_local float t_min_density = 0.02f;
 
 // Events of one profiled call: plan start, walk (kNumBins + 1), scan end,
-// gather end.
+// gather start and end, relabel start and end, re-ordering start and end.
 struct Events {
-  cudaEvent_t ev[kNumBins + 5] = {};
+  cudaEvent_t ev[kNumBins + 9] = {};
   bool on = false;
   explicit Events(bool enable) {
     if (!enable) return;
@@ -55,7 +56,8 @@ struct Events {
 };
 // Event slots.
 constexpr int kEvPlan = 0, kEvWalk = 1, kEvScan = kNumBins + 2, kEvGather0 = kNumBins + 3,
-              kEvGather1 = kNumBins + 4;
+              kEvGather1 = kNumBins + 4, kEvRelabel0 = kNumBins + 5, kEvRelabel1 = kNumBins + 6,
+              kEvOrder0 = kNumBins + 7, kEvOrder1 = kNumBins + 8;
 
 int status_of(cudaError_t e) {
   if (e == cudaSuccess) return SLG_OK;
@@ -106,8 +108,10 @@ int check_args(const slg_hypergraph *h, int32_t s, uint32_t flags) {
   const uint32_t algo = flags & SLG_ALGO_MASK;
   if (algo != SLG_ALGO_BINNED && algo != SLG_ALGO_PLAIN && algo != SLG_ALGO_SPGEMM)
     return SLG_ERR_UNSUPPORTED;
-  if (flags & ~(uint32_t)(SLG_DUAL | SLG_UNWEIGHTED | SLG_TENSOR_CORE | SLG_ALGO_MASK))
+  if (flags & ~(uint32_t)(SLG_DUAL | SLG_UNWEIGHTED | SLG_TENSOR_CORE | SLG_RELABEL_ASC |
+                          SLG_RELABEL_DESC | SLG_ALGO_MASK))
     return SLG_ERR_INVALID;
+  if ((flags & SLG_RELABEL_ASC) && (flags & SLG_RELABEL_DESC)) return SLG_ERR_INVALID;
   if ((flags & SLG_TENSOR_CORE) && algo != SLG_ALGO_BINNED) return SLG_ERR_UNSUPPORTED;
   return SLG_OK;
 }
@@ -282,8 +286,27 @@ int plan_core(Call &c, CoreInfo *core) {
   c.launches += 8;
   int32_t sizes[2] = {0, 0};
   SLG_TRY(cudaMemcpyAsync(&sizes[0], row_rank + sd.R, 4, cudaMemcpyDeviceToHost, c.st));
-  SLG_TRY(cudaMemcpyAsync(&sizes[1], col_rank + sd.C, 4, cudaMemcpyDeviceToHost, c.st));
   int rc = read_meta(c);
+  if (rc) return rc;
+  if (sizes[0] < 128) return SLG_OK;
+  // Refinement: the core columns are the columns where the core rows
+  // concentrate (at least max(8, min_density x |core rows|) of them); then the
+  // core rows are taken again against those columns.  This drops high-degree
+  // columns that the core rows hardly use.
+  {
+    int32_t *col_cnt;
+    SLG_TRY(c.pool->get(&col_cnt, (size_t)sd.C + 1));
+    const int32_t tau2 = std::max<int32_t>(8, (int32_t)std::ceil(t_min_density * sizes[0]));
+    SLG_TRY(launch_core_refine(sd, row_rank, col_cnt, tau2, core_col, w.meta, c.st));
+    SLG_TRY(launch_xscan(core_col, col_rank, (int64_t)sd.C + 1, tile, c.st));
+    SLG_TRY(cudaMemsetAsync(&w.meta->nnz_core, 0, sizeof(unsigned long long), c.st));
+    SLG_TRY(launch_core_rows(sd, t_tau_r, col_rank, core_row, &w.meta->nnz_core, w.meta, c.st));
+    SLG_TRY(launch_xscan(core_row, row_rank, (int64_t)sd.R + 1, tile, c.st));
+    c.launches += 7;
+  }
+  SLG_TRY(cudaMemcpyAsync(&sizes[0], row_rank + sd.R, 4, cudaMemcpyDeviceToHost, c.st));
+  SLG_TRY(cudaMemcpyAsync(&sizes[1], col_rank + sd.C, 4, cudaMemcpyDeviceToHost, c.st));
+  rc = read_meta(c);
   if (rc) return rc;
   const int64_t nR = sizes[0], nC = sizes[1];
   const int64_t nnz_core = (int64_t)c.meta_host->nnz_core;
@@ -585,6 +608,8 @@ int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin
   c.R_pad = (int32_t)(((int64_t)c.sd.R + 1023) / 1024 * 1024);
   if (c.R_pad == 0) c.R_pad = 1024;
   if (c.sd.R > kGiantMaxR) return SLG_ERR_UNSUPPORTED;
+  const uint32_t relabel = flags & (SLG_RELABEL_ASC | SLG_RELABEL_DESC);
+  if (relabel && (row_begin != 0 || row_end != c.sd.R || row_s)) return SLG_ERR_UNSUPPORTED;
 
   int dev = 0;
   DeviceCtx &ctx = ctx_for_current(&dev);
@@ -624,6 +649,29 @@ int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin
   SLG_TRY(launch_csr2csc(c.sd, w.csr2csc, w.meta, st));
   c.launches += 3;
 
+  // Degree-ordered relabelling: the rest of the call runs on a renumbered
+  // copy of the side (built only from input that passed validation).
+  int32_t *perm = nullptr;
+  if (relabel) {
+    rc = read_meta(c);
+    if (rc) return rc;
+    int32_t *r_off2, *r_idx2, *c_idx2, *scr;
+    SLG_TRY(pool.get(&perm, (size_t)c.sd.R + 1));
+    SLG_TRY(pool.get(&r_off2, (size_t)c.sd.R + 1));
+    SLG_TRY(pool.get(&r_idx2, (size_t)nnz + 1));
+    SLG_TRY(pool.get(&c_idx2, (size_t)nnz + 1));
+    SLG_TRY(pool.get(&scr, relabel_scratch_ints(c.sd.R, nnz)));
+    if (evs.on) cudaEventRecord(evs.ev[kEvRelabel0], st);
+    SLG_TRY(launch_relabel(c.sd, relabel == SLG_RELABEL_DESC, perm, r_off2, r_idx2, c_idx2, scr,
+                           st, &c.launches));
+    c.sd.r_off = r_off2;
+    c.sd.r_idx = r_idx2;
+    c.sd.c_idx = c_idx2;
+    SLG_TRY(launch_csr2csc(c.sd, w.csr2csc, w.meta, st));
+    if (evs.on) cudaEventRecord(evs.ev[kEvRelabel1], st);
+    c.launches += 1;
+  }
+
   int64_t value = 0;
   const uint32_t algo = flags & SLG_ALGO_MASK;
   if (algo == SLG_ALGO_PLAIN) rc = run_plain(c, &value);
@@ -631,6 +679,21 @@ int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin
   else rc = run_binned(c, &value);
   if (rc == SLG_OK || rc == SLG_ERR_CAPACITY) *result = value;
   if (rc != SLG_OK) return rc;
+
+  // Relabelled pairs -> caller ids in canonical (i, j) order.
+  if (perm && op == kOpBuild && value > 0) {
+    if (value >= ((int64_t)1 << 31)) return SLG_ERR_UNSUPPORTED;
+    unsigned long long *keys;
+    int32_t *vals = nullptr, *hist;
+    SLG_TRY(pool.get(&keys, 2 * (size_t)value));
+    if (!c.unweighted) SLG_TRY(pool.get(&vals, (size_t)value));
+    SLG_TRY(pool.get(&hist, radix_sort_scratch_ints(value)));
+    if (evs.on) cudaEventRecord(evs.ev[kEvOrder0], st);
+    SLG_TRY(launch_unrelabel(value, c.sd.R, perm, out_i, out_j, c.unweighted ? nullptr : out_w,
+                             keys, vals, hist, st, &c.launches));
+    if (evs.on) cudaEventRecord(evs.ev[kEvOrder1], st);
+    SLG_TRY(cudaStreamSynchronize(st));
+  }
 
   slg_stats stats = {};
   const Meta &m = *c.meta_host;
@@ -656,6 +719,10 @@ int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin
     for (int b = 0; b < kNumBins; ++b) stats.ms_walk[b] = evs.ms(kEvWalk + b, kEvWalk + b + 1);
     stats.ms_scan = evs.ms(kEvWalk + kNumBins, kEvScan);
     if (op == kOpBuild) stats.ms_gather = evs.ms(kEvGather0, kEvGather1);
+    if (perm) {
+      stats.ms_relabel = evs.ms(kEvRelabel0, kEvRelabel1);
+      if (op == kOpBuild && value > 0) stats.ms_order = evs.ms(kEvOrder0, kEvOrder1);
+    }
   }
   t_stats = stats;
   return SLG_OK;

@@ -10,9 +10,11 @@
 // tensor cores compute B_c·B_cᵀ (slg_tc.cu), and the two counts are added
 // before the threshold s.
 //
-// Core selection (degree thresholds): C_c = columns of degree >= tau_c;
-// R_c = rows with at least tau_r incidences in C_c.  Both are ranked in
-// ascending id order (scans), so the list of core rows is sorted.
+// Core selection (degree thresholds): candidate columns have degree >= tau_c,
+// candidate rows at least tau_r incidences in them; C_c = the columns holding
+// at least max(8, min_density x |rows|) candidate rows, R_c = the rows with at
+// least tau_r incidences in C_c.  Both are ranked in ascending id order
+// (scans), so the list of core rows is sorted.
 #include "slg_internal.cuh"
 
 namespace slg {
@@ -105,6 +107,28 @@ __global__ void k_core_xcsc(int32_t C, const int32_t *__restrict__ col_rank,
       out += __popc(bal);
     }
   }
+}
+
+// col_cnt[v] += 1 for every incidence (e, v) of a core row e (warp per row).
+__global__ void k_core_colcount(Side s, const int32_t *__restrict__ row_rank,
+                                int32_t *__restrict__ col_cnt, const Meta *meta) {
+  if (meta->err) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * kNT + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * kNT) >> 5;
+  for (int64_t e = gw; e < s.R; e += nw) {
+    if (row_rank[e + 1] == row_rank[e]) continue;
+    for (int32_t k = s.r_off[e] + lane; k < s.r_off[e + 1]; k += 32)
+      atomicAdd(col_cnt + s.r_idx[k], 1);
+  }
+}
+
+// core_col[v] = 1 if column v holds at least tau core rows (C + 1 entries).
+__global__ void k_core_cols_refine(int32_t C, const int32_t *__restrict__ col_cnt, int32_t tau,
+                                   int32_t *__restrict__ core_col) {
+  const int64_t v = (int64_t)blockIdx.x * kNT + threadIdx.x;
+  if (v > C) return;
+  core_col[v] = (v < C && col_cnt[v] >= tau) ? 1 : 0;
 }
 
 // Per core column: its number of non-core entries in the filtered CSC.
@@ -235,6 +259,16 @@ cudaError_t launch_core_rows(const Side &s, int32_t tau_r, const int32_t *col_ra
 cudaError_t launch_core_pack(const Side &s, const int32_t *row_rank, const int32_t *col_rank,
                              uint8_t *A, int32_t Kp, const Meta *meta, cudaStream_t st) {
   k_core_pack<<<grid_warps(s.R), kNT, 0, st>>>(s, row_rank, col_rank, A, Kp, meta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_core_refine(const Side &s, const int32_t *row_rank, int32_t *col_cnt,
+                               int32_t tau, int32_t *core_col, const Meta *meta,
+                               cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(col_cnt, 0, sizeof(int32_t) * ((size_t)s.C + 1), st);
+  if (e != cudaSuccess) return e;
+  k_core_colcount<<<grid_warps(s.R), kNT, 0, st>>>(s, row_rank, col_cnt, meta);
+  k_core_cols_refine<<<(int)((s.C + 1 + kNT - 1) / kNT), kNT, 0, st>>>(s.C, col_cnt, tau, core_col);
   return cudaGetLastError();
 }
 

@@ -288,6 +288,9 @@ cudaError_t launch_core_rows(const Side &s, int32_t tau_r, const int32_t *col_ra
                              cudaStream_t st);
 cudaError_t launch_core_list(int32_t R, const int32_t *row_rank, int32_t *core_list,
                              cudaStream_t st);
+cudaError_t launch_core_refine(const Side &s, const int32_t *row_rank, int32_t *col_cnt,
+                               int32_t tau, int32_t *core_col, const Meta *meta,
+                               cudaStream_t st);
 cudaError_t launch_core_pack(const Side &s, const int32_t *row_rank, const int32_t *col_rank,
                              uint8_t *A, int32_t Kp, const Meta *meta, cudaStream_t st);
 cudaError_t launch_core_xcount(int32_t C, const int32_t *col_rank, const int32_t *c_off_s,
@@ -373,6 +376,29 @@ cudaError_t launch_plain(const Side &sd, int32_t smin, int32_t row_begin, int32_
 cudaError_t launch_tile_overlap(const uint8_t *A, int32_t Mp, int32_t Kp, int32_t *C,
                                 void *tasks, int32_t *err, cudaStream_t st);
 size_t tile_overlap_smem();
+
+// Stable LSD radix sort (slg_sort.cu) by bits [begin_bit, end_bit) of the
+// keys, values alongside (vals may be null); tmp buffers of n entries,
+// hist of radix_sort_scratch_ints(n) ints; the result ends in keys / vals.
+// `launches` (optional) counts the kernels launched.
+size_t radix_sort_scratch_ints(int64_t n);
+cudaError_t launch_radix_sort(unsigned long long *keys, unsigned long long *keys_tmp,
+                              int32_t *vals, int32_t *vals_tmp, int64_t n, int begin_bit,
+                              int end_bit, int32_t *hist, cudaStream_t st,
+                              int32_t *launches = nullptr);
+cudaError_t launch_radix_sort(uint32_t *keys, uint32_t *keys_tmp, int32_t *vals,
+                              int32_t *vals_tmp, int64_t n, int begin_bit, int end_bit,
+                              int32_t *hist, cudaStream_t st, int32_t *launches = nullptr);
+
+// Degree-ordered relabelling (slg_relabel.cu).
+int relabel_row_bits(int32_t R);
+size_t relabel_scratch_ints(int32_t R, int64_t nnz);
+cudaError_t launch_relabel(const Side &sd, int descending, int32_t *perm, int32_t *r_off2,
+                           int32_t *r_idx2, int32_t *c_idx2, int32_t *scratch, cudaStream_t st,
+                           int32_t *launches);
+cudaError_t launch_unrelabel(int64_t P, int32_t R, const int32_t *perm, int32_t *out_i,
+                             int32_t *out_j, int32_t *out_w, unsigned long long *keys,
+                             int32_t *vals, int32_t *hist, cudaStream_t st, int32_t *launches);
 
 // Filtered SpGEMM comparison: full-column tails / per-row work, filtration.
 cudaError_t launch_rows_full(const Side &sd, int32_t row_begin, int32_t row_end,

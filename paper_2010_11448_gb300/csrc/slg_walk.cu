@@ -210,9 +210,16 @@ __device__ __forceinline__ int table_lg(int32_t distinct, int lg_max) {
 // qualify, and they are written to the front of the table.  A write of round
 // r lands below the number of qualifying slots seen so far, hence on a slot
 // of round r or earlier, all of which were read before the round's scan.
+#ifndef SLG_RANK_SORT_MAX
+#define SLG_RANK_SORT_MAX 512
+#endif
+constexpr int32_t kRankSortMax = SLG_RANK_SORT_MAX;
+
+// Returns the number of survivors; with `sort` they are in ascending f at
+// tab[*sorted_at, *sorted_at + count).
 template <int NT, int SPT>
 __device__ __forceinline__ int32_t table_collect(unsigned long long *tab, int32_t T, int32_t smin,
-                                                 bool sort, int32_t *ws) {
+                                                 bool sort, int32_t *ws, int32_t *sorted_at) {
   constexpr int RND = SPT < 8 ? SPT : 8;
   int32_t run = 0;
   for (int32_t r0 = 0; r0 * NT < T; r0 += RND) {
@@ -234,7 +241,21 @@ __device__ __forceinline__ int32_t table_collect(unsigned long long *tab, int32_
     }
     run += total;
   }
-  if (sort && run > 0) {
+  if (sort && run > 0 && run <= kRankSortMax) {
+    // Few survivors: place each one by its rank (the number of smaller keys;
+    // keys are distinct f, so ranks are a permutation) into tab[run, 2 run),
+    // which the table can hold (T >= 2 x distinct >= 2 x run).  Broadcast
+    // reads, no barrier inside the loop.
+    __syncthreads();
+    for (int32_t i = threadIdx.x; i < run; i += NT) {
+      const unsigned long long x = tab[i];
+      int32_t r = 0;
+      for (int32_t j = 0; j < run; ++j) r += tab[j] < x;
+      tab[run + r] = x;
+    }
+    __syncthreads();
+    *sorted_at = run;
+  } else if (sort && run > 0) {
     int32_t n2 = 1;
     while (n2 < run) n2 <<= 1;
     for (int32_t i = run + threadIdx.x; i < n2; i += NT) tab[i] = ~0ull;
@@ -254,6 +275,7 @@ __device__ __forceinline__ int32_t table_collect(unsigned long long *tab, int32_
         __syncthreads();
       }
     }
+    *sorted_at = 0;
   }
   return run;
 }
@@ -308,13 +330,14 @@ __global__ __launch_bounds__(NT, MINB) void k_walk_cta(Walk w, const int32_t *__
     cta_walk<NT, 4>(w, w.r_off[e], w.r_off[e + 1], s_beg, s_pref, ws, [&](int32_t f, int32_t) {
       table_insert(tab, lgT, f, 1, smin, unweighted, meta);
     });
-    const int32_t total = table_collect<NT, Cfg::kSPT>(tab, T, smin, emit, ws);
+    int32_t at = 0;
+    const int32_t total = table_collect<NT, Cfg::kSPT>(tab, T, smin, emit, ws, &at);
     if (threadIdx.x == 0) *s_base = reserve(a, e, total, BIN);
     __syncthreads();
     const long long base = *s_base;
     if (emit && base >= 0) {
       for (int32_t i = threadIdx.x; i < total; i += NT) {
-        const unsigned long long x = tab[i];
+        const unsigned long long x = tab[at + i];
         put(a, base, i, e, (int32_t)(x >> 32), (int32_t)(uint32_t)x);
       }
     }
@@ -620,7 +643,8 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
               table_insert(tab, lgT, f, wt, smin, unweighted, meta);
           }
         __syncthreads();
-        const int32_t total = table_collect<kGiantNT, kGiantSPT>(tab, T, smin, emit, ws);
+        int32_t at = 0;
+        const int32_t total = table_collect<kGiantNT, kGiantSPT>(tab, T, smin, emit, ws, &at);
         if (a.mode == kStage && out + total > q4) {
           // staged pairs would not fit the scratch (sized by wedges + core
           // items): report instead of writing past it
@@ -630,7 +654,7 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
         }
         if (emit && total > 0) {
           for (int32_t i = threadIdx.x; i < total; i += kGiantNT) {
-            const unsigned long long x = tab[i];
+            const unsigned long long x = tab[at + i];
             const int32_t f = (int32_t)(x >> 32), n = (int32_t)(uint32_t)x;
             if (a.mode == kDirect) {
               put(a, base, out + i, e, f, n);
