@@ -19,6 +19,7 @@
 // are appended to a staging area at an atomically reserved offset) and
 // DIRECT (written to their final place, row_ptr known).
 #include <mutex>
+#include <type_traits>
 
 #include "slg_internal.cuh"
 
@@ -169,24 +170,59 @@ __global__ __launch_bounds__(kWarpNT) void k_walk_warp(Walk w, const int32_t *__
 
 constexpr unsigned long long kEmpty64 = 0xFFFFFFFF00000000ull;
 
+// Survivor list (s >= 2): a key whose count reaches s during the inserts
+// appends its slot to `slot` (one extra shared atomic per surviving pair),
+// so collecting the survivors needs no pass over the table.  Counts only
+// grow, so each key crosses s exactly once.  `cap` bounds the list (a
+// survivor takes at least two wedges, or is one of at most T/2 keys).
+struct SurvList {
+  int32_t *slot;
+  int32_t *n;
+  int32_t cap;
+};
+
+__device__ __forceinline__ void note_survivor(const SurvList &sl, uint32_t h, int32_t old,
+                                              int32_t add, int32_t smin, Meta *meta) {
+  if (old < smin && old + add >= smin) {
+    const int32_t p = atomicAdd(sl.n, 1);
+    if (p < sl.cap) sl.slot[p] = (int32_t)h;
+    else raise_error(meta, SLG_ERR_INVALID, kWhereHash);  // unreachable by the bound
+  }
+}
+
+template <bool LIST>
+__device__ __forceinline__ void table_add(unsigned long long *tab, uint32_t h, int32_t add,
+                                          int32_t smin, Meta *meta, const SurvList &sl) {
+  if (LIST) {
+    const int32_t old = (int32_t)(uint32_t)atomicAdd(tab + h, (unsigned long long)add);
+    note_survivor(sl, h, old, add, smin, meta);
+  } else {
+    atomicAdd(tab + h, (unsigned long long)add);
+  }
+}
+
+template <bool LIST>
 __device__ __forceinline__ void table_insert(unsigned long long *tab, int lgT, int32_t f,
                                              int32_t add, int32_t smin, bool unweighted,
-                                             Meta *meta) {
+                                             Meta *meta, const SurvList &sl) {
   const uint32_t mask = (1u << lgT) - 1u;
   const unsigned long long key = (unsigned long long)(uint32_t)f << 32;
   uint32_t h = ((uint32_t)f * 0x9E3779B1u) >> (32 - lgT);
   for (uint32_t probe = 0; probe <= mask; ++probe) {
     const unsigned long long cur = *(volatile unsigned long long *)(tab + h);
     if ((cur & kEmpty64) == key) {
-      if (!unweighted || (int32_t)(uint32_t)cur < smin) atomicAdd(tab + h, (unsigned long long)add);
+      if (!unweighted || (int32_t)(uint32_t)cur < smin) table_add<LIST>(tab, h, add, smin, meta, sl);
       return;
     }
     if (cur == kEmpty64) {
       const unsigned long long prev = atomicCAS(tab + h, kEmpty64, key | (uint32_t)add);
-      if (prev == kEmpty64) return;
+      if (prev == kEmpty64) {
+        if (LIST) note_survivor(sl, h, 0, add, smin, meta);
+        return;
+      }
       if ((prev & kEmpty64) == key) {
         if (!unweighted || (int32_t)(uint32_t)prev < smin)
-          atomicAdd(tab + h, (unsigned long long)add);
+          table_add<LIST>(tab, h, add, smin, meta, sl);
         return;
       }
     }
@@ -205,16 +241,58 @@ __device__ __forceinline__ int table_lg(int32_t distinct, int lg_max) {
   return lg < lg_max ? lg : lg_max;
 }
 
-// Rounds of RND slots per thread (slot = (round * RND + i) * NT + thread):
-// a round reads its slots into registers, a block scan places the ones that
-// qualify, and they are written to the front of the table.  A write of round
-// r lands below the number of qualifying slots seen so far, hence on a slot
-// of round r or earlier, all of which were read before the round's scan.
 #ifndef SLG_RANK_SORT_MAX
 #define SLG_RANK_SORT_MAX 512
 #endif
 constexpr int32_t kRankSortMax = SLG_RANK_SORT_MAX;
 
+// Sorts keys[0, n) of the table region by f: by rank into [n, 2 n) when n
+// is small, else bitonic in place over [0, n2); returns where they are.
+// `*used` receives the end of the region touched.
+template <int NT>
+__device__ __forceinline__ int32_t sort_survivors(unsigned long long *tab, int32_t n,
+                                                  int32_t *used) {
+  if (n <= kRankSortMax) {
+    for (int32_t i = threadIdx.x; i < n; i += NT) {
+      const unsigned long long x = tab[i];
+      int32_t r = 0;
+      for (int32_t j = 0; j < n; ++j) r += tab[j] < x;
+      tab[n + r] = x;
+    }
+    __syncthreads();
+    *used = 2 * n;
+    return n;
+  }
+  int32_t n2 = 1;
+  while (n2 < n) n2 <<= 1;
+  for (int32_t i = n + threadIdx.x; i < n2; i += NT) tab[i] = ~0ull;
+  __syncthreads();
+  for (int32_t k = 2; k <= n2; k <<= 1) {
+    for (int32_t jj = k >> 1; jj > 0; jj >>= 1) {
+      for (int32_t i = threadIdx.x; i < n2; i += NT) {
+        const int32_t ixj = i ^ jj;
+        if (ixj > i) {
+          const unsigned long long x = tab[i], y = tab[ixj];
+          if ((x > y) == ((i & k) == 0)) {
+            tab[i] = y;
+            tab[ixj] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  *used = n2;
+  return 0;
+}
+
+// Survivors by a pass over the table (used for s = 1, where every key
+// survives).
+// Rounds of RND slots per thread (slot = (round * RND + i) * NT + thread):
+// a round reads its slots into registers, a block scan places the ones that
+// qualify, and they are written to the front of the table.  A write of round
+// r lands below the number of qualifying slots seen so far, hence on a slot
+// of round r or earlier, all of which were read before the round's scan.
 // Returns the number of survivors; with `sort` they are in ascending f at
 // tab[*sorted_at, *sorted_at + count).
 template <int NT, int SPT>
@@ -241,53 +319,53 @@ __device__ __forceinline__ int32_t table_collect(unsigned long long *tab, int32_
     }
     run += total;
   }
-  if (sort && run > 0 && run <= kRankSortMax) {
-    // Few survivors: place each one by its rank (the number of smaller keys;
-    // keys are distinct f, so ranks are a permutation) into tab[run, 2 run),
-    // which the table can hold (T >= 2 x distinct >= 2 x run).  Broadcast
-    // reads, no barrier inside the loop.
-    __syncthreads();
-    for (int32_t i = threadIdx.x; i < run; i += NT) {
-      const unsigned long long x = tab[i];
-      int32_t r = 0;
-      for (int32_t j = 0; j < run; ++j) r += tab[j] < x;
-      tab[run + r] = x;
-    }
-    __syncthreads();
-    *sorted_at = run;
-  } else if (sort && run > 0) {
-    int32_t n2 = 1;
-    while (n2 < run) n2 <<= 1;
-    for (int32_t i = run + threadIdx.x; i < n2; i += NT) tab[i] = ~0ull;
-    __syncthreads();
-    for (int32_t k = 2; k <= n2; k <<= 1) {
-      for (int32_t jj = k >> 1; jj > 0; jj >>= 1) {
-        for (int32_t i = threadIdx.x; i < n2; i += NT) {
-          const int32_t ixj = i ^ jj;
-          if (ixj > i) {
-            const unsigned long long x = tab[i], y = tab[ixj];
-            if ((x > y) == ((i & k) == 0)) {
-              tab[i] = y;
-              tab[ixj] = x;
-            }
-          }
-        }
-        __syncthreads();
-      }
-    }
-    *sorted_at = 0;
+  if (sort && run > 0) {
+    __syncthreads();  // compaction writes done
+    int32_t used;
+    *sorted_at = sort_survivors<NT>(tab, run, &used);
   }
   return run;
 }
 
-template <int NT, int SPT>
-__device__ __forceinline__ void table_reset(unsigned long long *tab, int32_t T) {
-  __syncthreads();  // sorted entries may still be read
+// Survivors from the list: read their (f, count) slots, clear the whole
+// table (plain stores), and with `sort` place them compactly at the front
+// and sort them.  Returns the number of survivors; with `sort` they are in
+// ascending f at tab[*sorted_at, + count) and tab[0, *used) must be cleared
+// after use (table_reset_front).  QMAX x NT >= the list's capacity.
+template <int NT, int QMAX>
+__device__ __forceinline__ int32_t table_collect_list(unsigned long long *tab, int32_t T,
+                                                      const SurvList &sl, bool sort,
+                                                      int32_t *sorted_at, int32_t *used) {
+  __syncthreads();  // every insert done: the list is final
+  const int32_t n = min(*sl.n, sl.cap);
+  unsigned long long x[QMAX];
 #pragma unroll
-  for (int i = 0; i < SPT; ++i) {
-    const int32_t slot = i * NT + (int32_t)threadIdx.x;
-    if (slot < T) tab[slot] = kEmpty64;
+  for (int q = 0; q < QMAX; ++q) {
+    const int32_t i = (int32_t)threadIdx.x + q * NT;
+    x[q] = (sort && i < n) ? tab[sl.slot[i]] : 0ull;
   }
+  __syncthreads();  // reads done before the table is cleared
+  for (int32_t i = threadIdx.x; i < T; i += NT) tab[i] = kEmpty64;
+  if (threadIdx.x == 0) *sl.n = 0;
+  __syncthreads();
+  *used = 0;
+  *sorted_at = 0;
+  if (!sort || n == 0) return n;
+#pragma unroll
+  for (int q = 0; q < QMAX; ++q) {
+    const int32_t i = (int32_t)threadIdx.x + q * NT;
+    if (i < n) tab[i] = x[q];
+  }
+  __syncthreads();
+  *sorted_at = sort_survivors<NT>(tab, n, used);
+  return n;
+}
+
+// Clears tab[0, used) after the survivors were emitted.
+template <int NT>
+__device__ __forceinline__ void table_reset_front(unsigned long long *tab, int32_t used) {
+  __syncthreads();  // sorted entries may still be read
+  for (int32_t i = threadIdx.x; i < used; i += NT) tab[i] = kEmpty64;
   __syncthreads();
 }
 
@@ -296,9 +374,13 @@ __device__ __forceinline__ void table_reset(unsigned long long *tab, int32_t T) 
 template <int NT, int TMAX>
 struct CtaCfg {
   static constexpr int kSPT = TMAX / NT;  // slots per thread at most
+  static constexpr int kList = TMAX / 4;  // survivors of a row when s >= 2 (<= work / 2)
+  static constexpr int kQ = (kList + NT - 1) / NT;
   // [s_base 16 B][table TMAX x 8 B][s_beg NT][s_pref NT+1][ws NT/32+1]
+  // [list kList][list count 1]
   static constexpr size_t smem() {
-    return 16 + (size_t)TMAX * 8 + (size_t)(2 * NT + 1 + NT / 32 + 1) * 4;
+    return 16 + (size_t)TMAX * 8 + (size_t)(2 * NT + 1 + NT / 32 + 1) * 4 +
+           (size_t)(kList + 1) * 4;
   }
 };
 
@@ -315,9 +397,11 @@ __global__ __launch_bounds__(NT, MINB) void k_walk_cta(Walk w, const int32_t *__
   int32_t *s_beg = reinterpret_cast<int32_t *>(tab + TMAX);
   int32_t *s_pref = s_beg + NT;
   int32_t *ws = s_pref + NT + 1;
+  const SurvList sl = {ws + NT / 32 + 1, ws + NT / 32 + 1 + Cfg::kList, Cfg::kList};
   constexpr int lg_max = (TMAX >= 2) ? 31 - __builtin_clz(TMAX) : 1;
 
   for (int i = threadIdx.x; i < TMAX; i += NT) tab[i] = kEmpty64;
+  if (threadIdx.x == 0) *sl.n = 0;
   __syncthreads();
   const long long nrows = (long long)meta->rows_bin[BIN];
   const bool unweighted = a.unweighted != 0;
@@ -327,11 +411,21 @@ __global__ __launch_bounds__(NT, MINB) void k_walk_cta(Walk w, const int32_t *__
     const int32_t smin = s_of(a.row_s, a.smin, e);
     const int lgT = table_lg(row_work[e - a.row_begin], lg_max);
     const int32_t T = 1 << lgT;
-    cta_walk<NT, 4>(w, w.r_off[e], w.r_off[e + 1], s_beg, s_pref, ws, [&](int32_t f, int32_t) {
-      table_insert(tab, lgT, f, 1, smin, unweighted, meta);
-    });
-    int32_t at = 0;
-    const int32_t total = table_collect<NT, Cfg::kSPT>(tab, T, smin, emit, ws, &at);
+    const int32_t k0 = w.r_off[e], k1 = w.r_off[e + 1];
+    int32_t at = 0, used = 0, total;
+    // s >= 2: survivors are listed as they appear; s = 1: every key survives
+    if (smin >= 2) {
+      cta_walk<NT, 4>(w, k0, k1, s_beg, s_pref, ws, [&](int32_t f, int32_t) {
+        table_insert<true>(tab, lgT, f, 1, smin, unweighted, meta, sl);
+      });
+      total = table_collect_list<NT, Cfg::kQ>(tab, T, sl, emit, &at, &used);
+    } else {
+      cta_walk<NT, 4>(w, k0, k1, s_beg, s_pref, ws, [&](int32_t f, int32_t) {
+        table_insert<false>(tab, lgT, f, 1, smin, unweighted, meta, sl);
+      });
+      total = table_collect<NT, Cfg::kSPT>(tab, T, smin, emit, ws, &at);
+      used = T;
+    }
     if (threadIdx.x == 0) *s_base = reserve(a, e, total, BIN);
     __syncthreads();
     const long long base = *s_base;
@@ -341,7 +435,7 @@ __global__ __launch_bounds__(NT, MINB) void k_walk_cta(Walk w, const int32_t *__
         put(a, base, i, e, (int32_t)(x >> 32), (int32_t)(uint32_t)x);
       }
     }
-    table_reset<NT, Cfg::kSPT>(tab, T);
+    table_reset_front<NT>(tab, used);
   }
 }
 
@@ -387,11 +481,14 @@ constexpr int kShiftMax = 31 - __builtin_clz(kGiantTMax / 4);  // 2^shift <= kGi
 constexpr int kGiantSPT = kGiantTMax / kGiantNT;
 constexpr int kDenseW = 2 * kGiantTMax;  // ids per dense window (int32 counters in the table)
 
+constexpr int kGiantList = kGiantTMax / 2;  // survivors of a bucket (<= its distinct keys)
+constexpr int kGiantQ = kGiantList / kGiantNT;
+
 // [s_base 16][s_misc 16][table TMAX x 8][sub NSB][subt NSB+1][bstart NSB+1]
-// [s_beg NT][s_pref NT+1][ws NT/32+1]
+// [s_beg NT][s_pref NT+1][ws NT/32+1][list kGiantList][list count 1]
 constexpr size_t giant_smem() {
   return 32 + (size_t)kGiantTMax * 8 + (size_t)(3 * kNSB + 2) * 4 +
-         (size_t)(2 * kGiantNT + 1 + kGiantNT / 32 + 1) * 4;
+         (size_t)(2 * kGiantNT + 1 + kGiantNT / 32 + 1) * 4 + (size_t)(kGiantList + 1) * 4;
 }
 
 // Exclusive scan of the kNSB sub-range counters in place (P per thread);
@@ -414,6 +511,25 @@ __device__ __forceinline__ int32_t scan_subranges(int32_t *a, int32_t *ws) {
   }
   __syncthreads();
   return total;
+}
+
+// fn(a[i]) for i = lo + threadIdx.x, lo + threadIdx.x + NT, ... < hi, with Q
+// loads issued together before their first use (the scratch reads are
+// latency-bound).
+template <int NT, int Q, class Fn>
+__device__ __forceinline__ void for_each_batched(const int32_t *a, int32_t lo, int32_t hi,
+                                                 Fn &&fn) {
+  for (int32_t i0 = lo + (int32_t)threadIdx.x; i0 < hi; i0 += Q * NT) {
+    int32_t v[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int32_t i = i0 + q * NT;
+      v[q] = i < hi ? a[i] : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+      if (i0 + q * NT < hi) fn(v[q]);
+  }
 }
 
 // First position p in core_list[0, n) with core_list[p] >= x.
@@ -442,6 +558,7 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
   int32_t *s_beg = bstart + kNSB + 1;
   int32_t *s_pref = s_beg + kGiantNT;
   int32_t *ws = s_pref + kGiantNT + 1;
+  const SurvList sl = {ws + kGiantNT / 32 + 1, ws + kGiantNT / 32 + 1 + kGiantList, kGiantList};
   // per-CTA global scratch, 4 ints per wedge of the largest row:
   // flattened far ends, far ends grouped by sub-range, staged pairs (j, w)
   const long long q4 = scratch_stride / 4;
@@ -451,6 +568,7 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
   int32_t *tw = tj + q4;
 
   for (int i = threadIdx.x; i < kGiantTMax; i += kGiantNT) tab[i] = kEmpty64;
+  if (threadIdx.x == 0) *sl.n = 0;
   const unsigned nrows = (unsigned)meta->rows_bin[kBinGiant];
   const bool unweighted = a.unweighted != 0;
   const bool emit = a.mode != kCount;
@@ -503,10 +621,9 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
         subt[i] = 0;
       }
       __syncthreads();
-      for (int32_t i = threadIdx.x; i < work; i += kGiantNT) {
-        const int32_t f = flat[i];
+      for_each_batched<kGiantNT, 8>(flat, 0, work, [&](int32_t f) {
         if (f >= F0 && f < F1) atomicAdd(sub + ((f - F0) >> shift), 1);
-      }
+      });
       if (core_row)
         for (int32_t p = ri + 1 + (int32_t)threadIdx.x; p < ci.n_core; p += kGiantNT) {
           const int32_t f = ci.core_list[p];
@@ -518,10 +635,9 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
       const int32_t items = core_row ? scan_subranges(subt, ws) : 0;
       if (nw == 0 && items == 0) continue;  // uniform: both totals are block-wide
       if (threadIdx.x == 0) subt[kNSB] = items;
-      for (int32_t i = threadIdx.x; i < work; i += kGiantNT) {
-        const int32_t f = flat[i];
+      for_each_batched<kGiantNT, 8>(flat, 0, work, [&](int32_t f) {
         if (f >= F0 && f < F1) wl[atomicAdd(sub + ((f - F0) >> shift), 1)] = f;
-      }
+      });
       __syncthreads();
       // now sub[b] = end of the wedges of sub-range b; subt[b] = start of its
       // items.  3. bucket starts: sub-range b opens a bucket when its start
@@ -581,8 +697,8 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
           int32_t *cnt = reinterpret_cast<int32_t *>(tab);
           for (int32_t i = threadIdx.x; i < dw; i += kGiantNT) cnt[i] = 0;
           __syncthreads();
-          for (int32_t i = lo + (int32_t)threadIdx.x; i < hi; i += kGiantNT)
-            atomicAdd(cnt + (wl[i] - fb0), 1);
+          for_each_batched<kGiantNT, 8>(wl, lo, hi,
+                                        [&](int32_t f) { atomicAdd(cnt + (f - fb0), 1); });
           if (core_row && nit > 0)
             for (int32_t p = s_misc[2] + (int32_t)threadIdx.x; p < s_misc[3]; p += kGiantNT) {
               const int32_t f = ci.core_list[p];
@@ -633,23 +749,35 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
         const int32_t width = (b1 - b0) << shift;
         const int lgT = table_lg(min(hi - lo + nit, width), lg_max);
         const int32_t T = 1 << lgT;
-        for (int32_t i = lo + (int32_t)threadIdx.x; i < hi; i += kGiantNT)
-          table_insert(tab, lgT, wl[i], 1, smin, unweighted, meta);
-        if (core_row && nit > 0)
-          for (int32_t p = s_misc[2] + (int32_t)threadIdx.x; p < s_misc[3]; p += kGiantNT) {
-            const int32_t f = ci.core_list[p];
-            const int32_t wt = Trow[p];
-            if (wt > 0 && w.r_off[f + 1] - w.r_off[f] >= smin)
-              table_insert(tab, lgT, f, wt, smin, unweighted, meta);
-          }
-        __syncthreads();
-        int32_t at = 0;
-        const int32_t total = table_collect<kGiantNT, kGiantSPT>(tab, T, smin, emit, ws, &at);
+        // s >= 2: survivors listed as they appear; s = 1: every key survives
+        const bool list = smin >= 2;
+        auto insert_all = [&](auto list_tag) {
+          constexpr bool L = decltype(list_tag)::value;
+          for_each_batched<kGiantNT, 8>(wl, lo, hi, [&](int32_t f) {
+            table_insert<L>(tab, lgT, f, 1, smin, unweighted, meta, sl);
+          });
+          if (core_row && nit > 0)
+            for (int32_t p = s_misc[2] + (int32_t)threadIdx.x; p < s_misc[3]; p += kGiantNT) {
+              const int32_t f = ci.core_list[p];
+              const int32_t wt = Trow[p];
+              if (wt > 0 && w.r_off[f + 1] - w.r_off[f] >= smin)
+                table_insert<L>(tab, lgT, f, wt, smin, unweighted, meta, sl);
+            }
+        };
+        int32_t at = 0, used = T, total;
+        if (list) {
+          insert_all(std::true_type{});
+          total = table_collect_list<kGiantNT, kGiantQ>(tab, T, sl, emit, &at, &used);
+        } else {
+          insert_all(std::false_type{});
+          __syncthreads();
+          total = table_collect<kGiantNT, kGiantSPT>(tab, T, smin, emit, ws, &at);
+        }
         if (a.mode == kStage && out + total > q4) {
           // staged pairs would not fit the scratch (sized by wedges + core
           // items): report instead of writing past it
           if (threadIdx.x == 0) raise_error(meta, SLG_ERR_INVALID, kWhereGiant);
-          table_reset<kGiantNT, kGiantSPT>(tab, T);
+          table_reset_front<kGiantNT>(tab, used);
           break;
         }
         if (emit && total > 0) {
@@ -665,7 +793,7 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
           }
         }
         out += total;
-        table_reset<kGiantNT, kGiantSPT>(tab, T);
+        table_reset_front<kGiantNT>(tab, used);
       }
       clk_bucket += clock64() - c1;
     }
