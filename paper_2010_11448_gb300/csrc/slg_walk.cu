@@ -163,10 +163,11 @@ __global__ __launch_bounds__(kWarpNT) void k_walk_warp(Walk w, const int32_t *__
 // An open-addressing table of T = 2^lgT 64-bit slots in shared memory, each
 // slot (f << 32 | count) for a far end f; kEmpty64 marks a free slot.  The
 // table holds at least twice the distinct keys it will receive, so it never
-// fills.  A new key costs one CAS, a repeated one a load and an add.  After
-// the walk, table_collect counts the slots with count >= s and, if asked,
-// moves them to the front of the table (they are already packed as sort keys)
-// and sorts them by f.
+// fills.  A new key costs one 64-bit CAS, a repeated one a 32-bit add to the
+// slot's count word.  After the walk the slots with count >= s (found
+// from the survivor list for s >= 2, by a pass over the table for s = 1) are
+// moved to the front of the table, already packed as sort keys, and sorted
+// by f.
 
 constexpr unsigned long long kEmpty64 = 0xFFFFFFFF00000000ull;
 
@@ -190,17 +191,27 @@ __device__ __forceinline__ void note_survivor(const SurvList &sl, uint32_t h, in
   }
 }
 
+// A new key claims its slot with one 64-bit CAS that also sets its first
+// count; a repeated key adds to the slot's count word (the low 32 bits) with
+// a 32-bit atomic add, several times faster than a 64-bit one on this GPU.
+__device__ __forceinline__ uint32_t *count_word(unsigned long long *tab, uint32_t h) {
+  return reinterpret_cast<uint32_t *>(tab + h);
+}
+
 template <bool LIST>
-__device__ __forceinline__ void table_add(unsigned long long *tab, uint32_t h, int32_t add,
+__device__ __forceinline__ void count_add(unsigned long long *tab, uint32_t h, int32_t add,
                                           int32_t smin, Meta *meta, const SurvList &sl) {
   if (LIST) {
-    const int32_t old = (int32_t)(uint32_t)atomicAdd(tab + h, (unsigned long long)add);
+    const int32_t old = (int32_t)atomicAdd(count_word(tab, h), (uint32_t)add);
     note_survivor(sl, h, old, add, smin, meta);
   } else {
-    atomicAdd(tab + h, (unsigned long long)add);
+    atomicAdd(count_word(tab, h), (uint32_t)add);
   }
 }
 
+// With the survivor list (s >= 2, mostly new keys: sparse rows) a probe
+// starts with the CAS itself; otherwise with a read, which spares repeated
+// keys the CAS.  Unweighted: a count that reached s is not raised further.
 template <bool LIST>
 __device__ __forceinline__ void table_insert(unsigned long long *tab, int lgT, int32_t f,
                                              int32_t add, int32_t smin, bool unweighted,
@@ -209,22 +220,17 @@ __device__ __forceinline__ void table_insert(unsigned long long *tab, int lgT, i
   const unsigned long long key = (unsigned long long)(uint32_t)f << 32;
   uint32_t h = ((uint32_t)f * 0x9E3779B1u) >> (32 - lgT);
   for (uint32_t probe = 0; probe <= mask; ++probe) {
-    const unsigned long long cur = *(volatile unsigned long long *)(tab + h);
-    if ((cur & kEmpty64) == key) {
-      if (!unweighted || (int32_t)(uint32_t)cur < smin) table_add<LIST>(tab, h, add, smin, meta, sl);
-      return;
-    }
+    unsigned long long cur = LIST ? kEmpty64 : *(volatile unsigned long long *)(tab + h);
     if (cur == kEmpty64) {
-      const unsigned long long prev = atomicCAS(tab + h, kEmpty64, key | (uint32_t)add);
-      if (prev == kEmpty64) {
+      cur = atomicCAS(tab + h, kEmpty64, key | (uint32_t)add);
+      if (cur == kEmpty64) {
         if (LIST) note_survivor(sl, h, 0, add, smin, meta);
         return;
       }
-      if ((prev & kEmpty64) == key) {
-        if (!unweighted || (int32_t)(uint32_t)prev < smin)
-          table_add<LIST>(tab, h, add, smin, meta, sl);
-        return;
-      }
+    }
+    if ((cur & kEmpty64) == key) {
+      if (!unweighted || (int32_t)(uint32_t)cur < smin) count_add<LIST>(tab, h, add, smin, meta, sl);
+      return;
     }
     h = (h + 1) & mask;
   }
