@@ -163,8 +163,8 @@ __global__ __launch_bounds__(kWarpNT) void k_walk_warp(Walk w, const int32_t *__
 // An open-addressing table of T = 2^lgT 64-bit slots in shared memory, each
 // slot (f << 32 | count) for a far end f; kEmpty64 marks a free slot.  The
 // table holds at least twice the distinct keys it will receive, so it never
-// fills.  A new key costs one 64-bit CAS, a repeated one a 32-bit add to the
-// slot's count word.  After the walk the slots with count >= s (found
+// fills.  A new key costs one CAS, a repeated one a 32-bit add to the slot's
+// count word (see table_insert).  After the walk the slots with count >= s (found
 // from the survivor list for s >= 2, by a pass over the table for s = 1) are
 // moved to the front of the table, already packed as sort keys, and sorted
 // by f.
@@ -191,27 +191,21 @@ __device__ __forceinline__ void note_survivor(const SurvList &sl, uint32_t h, in
   }
 }
 
-// A new key claims its slot with one 64-bit CAS that also sets its first
-// count; a repeated key adds to the slot's count word (the low 32 bits) with
-// a 32-bit atomic add, several times faster than a 64-bit one on this GPU.
+// The count word of slot h: its low 32 bits (the key word is the high half).
+// Counts grow by 32-bit atomic adds, several times faster than 64-bit ones
+// in shared memory on this GPU.
 __device__ __forceinline__ uint32_t *count_word(unsigned long long *tab, uint32_t h) {
   return reinterpret_cast<uint32_t *>(tab + h);
 }
 
-template <bool LIST>
-__device__ __forceinline__ void count_add(unsigned long long *tab, uint32_t h, int32_t add,
-                                          int32_t smin, Meta *meta, const SurvList &sl) {
-  if (LIST) {
-    const int32_t old = (int32_t)atomicAdd(count_word(tab, h), (uint32_t)add);
-    note_survivor(sl, h, old, add, smin, meta);
-  } else {
-    atomicAdd(count_word(tab, h), (uint32_t)add);
-  }
-}
-
-// With the survivor list (s >= 2, mostly new keys: sparse rows) a probe
-// starts with the CAS itself; otherwise with a read, which spares repeated
-// keys the CAS.  Unweighted: a count that reached s is not raised further.
+// Inserts `add` wedges to far end f.  Unweighted: a count that reached s is
+// not raised further.
+//  - With the survivor list (s >= 2; mostly new keys in sparse rows) the key
+//    word alone is claimed with a 32-bit CAS and the claim itself stands for
+//    one wedge: the count word holds count - 1 (table_collect_list adds the
+//    1 back).  A repeated key adds to the count word.
+//  - Otherwise a probe reads the slot first (sparing repeated keys the CAS)
+//    and a new key is claimed with one 64-bit CAS that also sets its count.
 template <bool LIST>
 __device__ __forceinline__ void table_insert(unsigned long long *tab, int lgT, int32_t f,
                                              int32_t add, int32_t smin, bool unweighted,
@@ -220,16 +214,32 @@ __device__ __forceinline__ void table_insert(unsigned long long *tab, int lgT, i
   const unsigned long long key = (unsigned long long)(uint32_t)f << 32;
   uint32_t h = ((uint32_t)f * 0x9E3779B1u) >> (32 - lgT);
   for (uint32_t probe = 0; probe <= mask; ++probe) {
-    unsigned long long cur = LIST ? kEmpty64 : *(volatile unsigned long long *)(tab + h);
-    if (cur == kEmpty64) {
-      cur = atomicCAS(tab + h, kEmpty64, key | (uint32_t)add);
-      if (cur == kEmpty64) {
-        if (LIST) note_survivor(sl, h, 0, add, smin, meta);
+    if (LIST) {
+      uint32_t *cw = count_word(tab, h);
+      const uint32_t k = atomicCAS(cw + 1, 0xFFFFFFFFu, (uint32_t)f);  // key word
+      if (k == 0xFFFFFFFFu) {  // claimed: count 1 so far
+        if (add > 1) {
+          const int32_t old = (int32_t)atomicAdd(cw, (uint32_t)(add - 1));
+          note_survivor(sl, h, old + 1, add - 1, smin, meta);
+        }
         return;
       }
+      if (k == (uint32_t)f) {
+        if (unweighted && (int32_t)*(volatile uint32_t *)cw + 1 >= smin) return;
+        const int32_t old = (int32_t)atomicAdd(cw, (uint32_t)add);
+        note_survivor(sl, h, old + 1, add, smin, meta);
+        return;
+      }
+      h = (h + 1) & mask;
+      continue;
+    }
+    unsigned long long cur = *(volatile unsigned long long *)(tab + h);
+    if (cur == kEmpty64) {
+      cur = atomicCAS(tab + h, kEmpty64, key | (uint32_t)add);
+      if (cur == kEmpty64) return;
     }
     if ((cur & kEmpty64) == key) {
-      if (!unweighted || (int32_t)(uint32_t)cur < smin) count_add<LIST>(tab, h, add, smin, meta, sl);
+      if (!unweighted || (int32_t)(uint32_t)cur < smin) atomicAdd(count_word(tab, h), (uint32_t)add);
       return;
     }
     h = (h + 1) & mask;
@@ -348,7 +358,7 @@ __device__ __forceinline__ int32_t table_collect_list(unsigned long long *tab, i
 #pragma unroll
   for (int q = 0; q < QMAX; ++q) {
     const int32_t i = (int32_t)threadIdx.x + q * NT;
-    x[q] = (sort && i < n) ? tab[sl.slot[i]] : 0ull;
+    x[q] = (sort && i < n) ? tab[sl.slot[i]] + 1ull : 0ull;  // count word holds count - 1
   }
   __syncthreads();  // reads done before the table is cleared
   for (int32_t i = threadIdx.x; i < T; i += NT) tab[i] = kEmpty64;
