@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (testing)")
     ap.add_argument("--builds", default="all",
                     help="comma list of builds to run, e.g. 'H:8,H*:2' (profiling)")
-    ap.add_argument("--mode", choices=["headline", "batch", "serve", "core"], default="headline",
+    ap.add_argument("--mode", choices=["headline", "batch", "serve", "core", "sweep", "ablation"],
+                    default="headline",
                     help="headline: the Chung-Lu build (default); batch: many hypergraphs "
                          "in one captured pipeline vs sequential builds; serve: Poisson "
                          "query stream; core: planted dense core with and without the "
@@ -67,6 +68,7 @@ def parse():
     ap.add_argument("--queries", type=int, default=2000)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--core-scale", type=float, default=1.0)
+    ap.add_argument("--ablation-scale", type=float, default=0.25)
     return ap.parse_args()
 
 
@@ -601,6 +603,94 @@ def run_core(args):
     return 0
 
 
+SWEEP_S = (2, 3, 4, 6, 8, 12, 16)
+
+
+def run_sweep(args):
+    """s-sweep on the headline workload: L_s for s in SWEEP_S on H and H*,
+    from one walk at s = 2 plus filters (slg_build_sweep), against one
+    independent build per threshold (same outputs, checked)."""
+    torch, slg = _setup_gpu()
+    h = make_workload(0, args.scale)
+    dh = slg.to_device(h)
+    rows = {}
+    for dual in (False, True):
+        caps = [slg.count(dh, s, dual) for s in SWEEP_S]
+        outs = [slg.alloc_outputs(c) for c in caps]
+        ind = [slg.alloc_outputs(c) for c in caps]
+
+        def sweep():
+            return slg.build_sweep(dh, SWEEP_S, dual=dual, outs=outs)
+
+        def separate():
+            return [slg.build(dh, s, dual=dual, out=o) for s, o in zip(SWEEP_S, ind)]
+        res = {}
+        for name, fn in (("sweep", sweep), ("separate", separate)):
+            fn()
+            best = None
+            for _ in range(3):
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                fn()
+                torch.cuda.synchronize()
+                ms = (time.perf_counter() - t) * 1e3
+                best = ms if best is None or ms < best else best
+            res[name + "_ms"] = best
+        a, b = sweep(), separate()
+        res["identical"] = all(torch.equal(x, y) for p, q in zip(a, b) for x, y in zip(p, q))
+        res["pairs"] = dict(zip([str(s) for s in SWEEP_S], caps))
+        res["speedup"] = res["separate_ms"] / res["sweep_ms"]
+        rows["H*" if dual else "H"] = res
+    print(json.dumps({"mode": "sweep", "metric": "L_s for s in " + str(list(SWEEP_S)) +
+                      ": one walk + filters vs one build per s, ms",
+                      "workload": WORKLOAD_TEXT, "sides": rows}), flush=True)
+    return 0
+
+
+ABLATION = [("f0 all heuristics", dict(unweighted=True)),
+            ("f1 degree pruning", dict()),
+            ("f2 visited skip only", dict(prune=False)),
+            ("f3 short-circuit only", dict(prune=False, unweighted=True)),
+            ("f4 none (filtered SpGEMM)", dict(algo="spgemm"))]
+
+
+def run_ablation(args):
+    """GPU analogue of the heuristic ablation of Section V (Table 3, Fig. 6):
+    build ms and wedges walked per variant at s = 2, 4, 6, 8 on H and H* of the
+    Chung-Lu workload scaled by --ablation-scale; every variant's pair list is
+    checked against f1's."""
+    torch, slg = _setup_gpu()
+    h = make_workload(0, args.ablation_scale)
+    dh = slg.to_device(h)
+    rows = {}
+    for dual in (False, True):
+        for s in (2, 4, 6, 8):
+            n = slg.count(dh, s, dual)
+            ref = slg.build(dh, s, dual=dual)
+            res = {}
+            for name, kw in ABLATION:
+                out = slg.alloc_outputs(n, unweighted=kw.get("unweighted", False))
+                slg.build(dh, s, dual=dual, out=out, **kw)
+                best = None
+                for _ in range(2):
+                    torch.cuda.synchronize()
+                    t = time.perf_counter()
+                    got = slg.build(dh, s, dual=dual, out=out, **kw)
+                    torch.cuda.synchronize()
+                    ms = (time.perf_counter() - t) * 1e3
+                    best = ms if best is None or ms < best else best
+                same = torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1]) and (
+                    got[2] is None or torch.equal(got[2], ref[2]))
+                res[name] = {"ms": best, "wedges": slg.last_stats()["wedges"], "same": same}
+                del out, got
+            rows[f"{'H*' if dual else 'H'} s={s}"] = res
+            del ref
+    print(json.dumps({"mode": "ablation", "metric": "build ms per heuristic variant",
+                      "m": h.m, "n": h.n, "nnz": h.nnz, "scale": args.ablation_scale,
+                      "builds": rows}), flush=True)
+    return 0
+
+
 def main():
     global _ONLY
     args = parse()
@@ -617,6 +707,10 @@ def main():
         return run_serve(args)
     if args.mode == "core":
         return run_core(args)
+    if args.mode == "sweep":
+        return run_sweep(args)
+    if args.mode == "ablation":
+        return run_ablation(args)
     return run_ours(args)
 
 

@@ -97,6 +97,11 @@ typedef enum slg_status {
                                 2^31 for slg_build. */
 #define SLG_RELABEL_DESC 0x10u /* the same by descending size; at most one
                                   of the two relabel flags */
+#define SLG_NO_PRUNE 0x20u   /* switch off the degree-based pruning of
+                                Algorithm 3 (rows of size < s stay in the
+                                walk at both ends): same result, more work.
+                                For ablations (Section V); binned algorithm
+                                only */
 /* Algorithm selector (mutually exclusive values in bits 8..11). */
 #define SLG_ALGO_MASK 0xF00u
 #define SLG_ALGO_BINNED 0x000u /* default: degree-binned wedge walk */
@@ -112,7 +117,7 @@ typedef enum slg_status {
  *   h        incidence of H (device arrays as described above)
  *   s        overlap threshold, s >= 1 (s larger than every hyperedge gives 0)
  *   flags    SLG_DUAL, SLG_UNWEIGHTED, SLG_TENSOR_CORE, SLG_RELABEL_ASC or
- *            SLG_RELABEL_DESC, one SLG_ALGO_* value
+ *            SLG_RELABEL_DESC, SLG_NO_PRUNE, one SLG_ALGO_* value
  *   n_pairs  host pointer, receives |L_s|
  *   stream   cudaStream_t to run on
  * Returns SLG_OK, SLG_ERR_INVALID (s < 1, NULL pointers, negative sizes,
@@ -167,6 +172,48 @@ int slg_build_host(const slg_hypergraph *h, int32_t s, uint32_t flags,
  */
 int slg_wedges(const slg_hypergraph *h, int32_t s, uint32_t flags,
                int64_t *wedges, void *stream);
+
+/*
+ * slg_filter -- L_s from the canonical edge list of L_s' for any s' <= s:
+ * the triples with w >= s, in the same order (Section III: L_s keeps the
+ * overlaps of weight >= s, so L_s ⊆ L_s' with equal weights).
+ *   in_i, in_j, in_w     device arrays of n triples (a canonical edge list,
+ *                        weighted); only read
+ *   s                    threshold >= 1
+ *   out_i, out_j, out_w  device arrays of `capacity` entries, not
+ *                        overlapping the inputs; out_w may be NULL (weights
+ *                        not written)
+ *   n_pairs              host pointer, receives the kept count
+ * Returns SLG_OK, SLG_ERR_INVALID, SLG_ERR_CAPACITY (*n_pairs = the kept
+ * count, outputs unspecified), SLG_ERR_NOMEM, SLG_ERR_CUDA.
+ */
+int slg_filter(const int32_t *in_i, const int32_t *in_j, const int32_t *in_w,
+               int64_t n, int32_t s, int32_t *out_i, int32_t *out_j,
+               int32_t *out_w, int64_t capacity, int64_t *n_pairs,
+               void *stream);
+
+/*
+ * slg_build_sweep -- L_s for `count` thresholds with one walk: L_{s_min}
+ * (the smallest threshold) is built by slg_build, every other list is
+ * filtered from it (slg_filter).
+ *   s          HOST array of `count` thresholds (>= 1, any order), 1..64
+ *   flags      as for slg_build except SLG_UNWEIGHTED (SLG_ERR_UNSUPPORTED:
+ *              the weights decide membership)
+ *   out_i, out_j, out_w   HOST arrays of `count` device pointers; list k
+ *              receives L_{s[k]}.  out_w of the smallest threshold is
+ *              required (the other lists are filtered by it); the others
+ *              may be NULL
+ *   capacity   HOST array of `count` capacities
+ *   n_pairs    HOST array of `count` results; -1 where not computed
+ * If the smallest threshold's list does not fit, returns SLG_ERR_CAPACITY
+ * with only its count set.  If another list does not fit, every count is
+ * set, the lists that fit are written, and SLG_ERR_CAPACITY is returned.
+ * slg_last_stats describes the walk.  Other errors as for slg_build.
+ */
+int slg_build_sweep(const slg_hypergraph *h, const int32_t *s, int32_t count,
+                    uint32_t flags, int32_t *const *out_i,
+                    int32_t *const *out_j, int32_t *const *out_w,
+                    const int64_t *capacity, int64_t *n_pairs, void *stream);
 
 /*
  * slg_tile_overlap -- exact overlap counts of a dense 0/1 block on the

@@ -21,7 +21,9 @@ import numpy as np
 __all__ = [
     "DeviceHypergraph", "to_device", "count", "build", "build_rows",
     "build_host", "wedges", "last_stats", "set_profiling", "tile_overlap",
+    "filter_pairs", "build_sweep",
     "set_core_params", "SLG_TENSOR_CORE", "SLG_RELABEL_ASC", "SLG_RELABEL_DESC",
+    "SLG_NO_PRUNE",
     "Plan", "alloc_outputs",
     "library_path", "load",
     "SLG_DUAL", "SLG_UNWEIGHTED", "SLG_ALGO_BINNED", "SLG_ALGO_PLAIN",
@@ -33,6 +35,7 @@ SLG_UNWEIGHTED = 0x2
 SLG_TENSOR_CORE = 0x4
 SLG_RELABEL_ASC = 0x8
 SLG_RELABEL_DESC = 0x10
+SLG_NO_PRUNE = 0x20
 SLG_ALGO_BINNED = 0x000
 SLG_ALGO_PLAIN = 0x100
 SLG_ALGO_SPGEMM = 0x200
@@ -104,6 +107,10 @@ ABI_FUNCTIONS = {
     "slg_set_profiling": (ctypes.c_int, [ctypes.c_int]),
     "slg_set_core_params": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_float]),
     "slg_tile_overlap": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP]),
+    "slg_filter": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int32, _VP, _VP,
+                                  _VP, ctypes.c_int64, _I64P, _VP]),
+    "slg_build_sweep": (ctypes.c_int, [_HP, _VP, ctypes.c_int32, ctypes.c_uint32, _VP, _VP,
+                                       _VP, _VP, _VP, _VP]),
     "slg_plan_create": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, ctypes.c_uint32,
                                        ctypes.POINTER(ctypes.c_void_p), _VP]),
     "slg_plan_execute": (ctypes.c_int, [_VP, _VP]),
@@ -182,8 +189,8 @@ def to_device(h, device="cuda") -> DeviceHypergraph:
     return DeviceHypergraph(h.m, h.n, t(h.e_off), t(h.e_idx), t(h.v_off), t(h.v_idx))
 
 
-def _flags(dual, unweighted, algo, tensor=False, relabel=None):
-    f = _ALGOS[algo] | _RELABEL[relabel]
+def _flags(dual, unweighted, algo, tensor=False, relabel=None, prune=True):
+    f = _ALGOS[algo] | _RELABEL[relabel] | (0 if prune else SLG_NO_PRUNE)
     if tensor:
         f |= SLG_TENSOR_CORE
     if dual:
@@ -201,11 +208,11 @@ def _stream(stream):
 
 
 def count(h: DeviceHypergraph, s: int, dual=False, unweighted=False,
-          algo="binned", stream=None, tensor=False, relabel=None) -> int:
+          algo="binned", stream=None, tensor=False, relabel=None, prune=True) -> int:
     """|L_s(H)| (or of H* with dual=True)."""
     n = ctypes.c_int64(0)
     rc = load().slg_count(ctypes.byref(h.struct), int(s),
-                          _flags(dual, unweighted, algo, tensor, relabel),
+                          _flags(dual, unweighted, algo, tensor, relabel, prune),
                           ctypes.byref(n), _stream(stream))
     if rc != 0:
         raise SlgError(rc, "slg_count")
@@ -228,13 +235,14 @@ def _outputs(capacity, unweighted, device):
 
 def build(h: DeviceHypergraph, s: int, dual=False, unweighted=False,
           algo="binned", capacity=None, out=None, stream=None, tensor=False,
-          relabel=None):
+          relabel=None, prune=True):
     """The canonical edge list of L_s as int32 tensors (i, j, w); w is None
     with unweighted=True.  Without ``capacity``/``out`` the pair count is
     taken first with ``count`` (an extra walk).  tensor=True counts a dense
     core block on the tensor cores; relabel="asc"/"desc" renumbers the rows
-    by size for the walk (both give the same result)."""
-    flags = _flags(dual, unweighted, algo, tensor, relabel)
+    by size for the walk; prune=False switches off the degree-based pruning
+    (all give the same result)."""
+    flags = _flags(dual, unweighted, algo, tensor, relabel, prune)
     if out is None:
         if capacity is None:
             capacity = count(h, s, dual, unweighted, algo, stream, tensor)
@@ -312,6 +320,60 @@ def wedges(h: DeviceHypergraph, s: int, dual=False, stream=None) -> int:
     if rc != 0:
         raise SlgError(rc, "slg_wedges")
     return int(n.value)
+
+
+def filter_pairs(i, j, w, s: int, out=None, stream=None, weights=True):
+    """L_s from a canonical weighted edge list (i, j, w) of any L_s' with
+    s' <= s: the triples with w >= s, in order (slg_filter)."""
+    n = int(i.shape[0])
+    if out is None:
+        cnt = ctypes.c_int64(0)
+        rc = load().slg_filter(i.data_ptr(), j.data_ptr(), w.data_ptr(), n, int(s), None, None,
+                               None, 0, ctypes.byref(cnt), _stream(stream))
+        if rc not in (0, SLG_ERR_CAPACITY):
+            raise SlgError(rc, "slg_filter")
+        out = _outputs(cnt.value, not weights, i.device)
+    oi, oj, ow = out
+    cnt = ctypes.c_int64(0)
+    rc = load().slg_filter(i.data_ptr(), j.data_ptr(), w.data_ptr(), n, int(s), oi.data_ptr(),
+                           oj.data_ptr(), ow.data_ptr() if ow is not None else None,
+                           int(oi.shape[0]), ctypes.byref(cnt), _stream(stream))
+    if rc != 0:
+        err = SlgError(rc, "slg_filter")
+        err.needed = int(cnt.value)
+        raise err
+    p = int(cnt.value)
+    return oi[:p], oj[:p], (ow[:p] if ow is not None else None)
+
+
+def build_sweep(h: DeviceHypergraph, s_list, dual=False, algo="binned", outs=None,
+                stream=None, tensor=False, relabel=None):
+    """L_s for every s in s_list from one walk at min(s_list) (slg_build_sweep).
+    ``outs``: one (i, j, w) tensor triple per threshold; without it the lists
+    are sized by slg_count at each threshold.  Returns a list of triples."""
+    s_list = [int(x) for x in s_list]
+    k = len(s_list)
+    if outs is None:
+        outs = [_outputs(count(h, x, dual, False, algo, stream, tensor), False, h.e_off.device)
+                for x in s_list]
+    arr = lambda vals, t: (t * k)(*vals)
+    oi = arr([o[0].data_ptr() for o in outs], ctypes.c_void_p)
+    oj = arr([o[1].data_ptr() for o in outs], ctypes.c_void_p)
+    ow = arr([o[2].data_ptr() if o[2] is not None else None for o in outs], ctypes.c_void_p)
+    cap = arr([int(o[0].shape[0]) for o in outs], ctypes.c_int64)
+    np_ = (ctypes.c_int64 * k)()
+    sv = arr(s_list, ctypes.c_int32)
+    rc = load().slg_build_sweep(ctypes.byref(h.struct), sv, k,
+                                _flags(dual, False, algo, tensor, relabel), oi, oj, ow, cap,
+                                np_, _stream(stream))
+    if rc != 0:
+        err = SlgError(rc, "slg_build_sweep")
+        err.needed = list(np_)
+        raise err
+    res = []
+    for (a, b, c), p in zip(outs, list(np_)):
+        res.append((a[:p], b[:p], c[:p] if c is not None else None))
+    return res
 
 
 def last_stats() -> dict:

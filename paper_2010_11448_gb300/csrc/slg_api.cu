@@ -109,8 +109,9 @@ int check_args(const slg_hypergraph *h, int32_t s, uint32_t flags) {
   if (algo != SLG_ALGO_BINNED && algo != SLG_ALGO_PLAIN && algo != SLG_ALGO_SPGEMM)
     return SLG_ERR_UNSUPPORTED;
   if (flags & ~(uint32_t)(SLG_DUAL | SLG_UNWEIGHTED | SLG_TENSOR_CORE | SLG_RELABEL_ASC |
-                          SLG_RELABEL_DESC | SLG_ALGO_MASK))
+                          SLG_RELABEL_DESC | SLG_NO_PRUNE | SLG_ALGO_MASK))
     return SLG_ERR_INVALID;
+  if ((flags & SLG_NO_PRUNE) && algo != SLG_ALGO_BINNED) return SLG_ERR_UNSUPPORTED;
   if ((flags & SLG_RELABEL_ASC) && (flags & SLG_RELABEL_DESC)) return SLG_ERR_INVALID;
   if ((flags & SLG_TENSOR_CORE) && algo != SLG_ALGO_BINNED) return SLG_ERR_UNSUPPORTED;
   return SLG_OK;
@@ -358,13 +359,17 @@ int plan_core(Call &c, CoreInfo *core) {
 // Default path: filtered CSC, binned single walk, staging, scan, gather.
 int run_binned(Call &c, int64_t *result) {
   Work &w = c.w;
-  SLG_TRY(launch_filter(c.sd, c.smin, w, c.st));
+  // Degree-based pruning (Alg. 3) drops rows of size < s from both ends of
+  // the walk; SLG_NO_PRUNE keeps them (the threshold still applies to the
+  // counts, and such rows cannot reach it).
+  const int32_t s_prune = (c.flags & SLG_NO_PRUNE) ? 1 : c.smin;
+  SLG_TRY(launch_filter(c.sd, s_prune, w, c.st));
   CoreInfo core = {};
   if (c.flags & SLG_TENSOR_CORE) {
     const int rcc = plan_core(c, &core);
     if (rcc) return rcc;
   }
-  SLG_TRY(launch_rows_work(c.sd, c.smin, c.row_begin, c.row_end, w, core, t_bins, c.st));
+  SLG_TRY(launch_rows_work(c.sd, s_prune, c.row_begin, c.row_end, w, core, t_bins, c.st));
   c.launches += 4 + (c.rows > 0 ? 1 : 0);
   if (c.op == kOpWedges) {
     int rc = read_meta(c);
@@ -918,6 +923,80 @@ int slg_build_host(const slg_hypergraph *hh, int32_t s, uint32_t flags, int32_t 
   }
   SLG_TRY(cudaStreamSynchronize(st));
   return SLG_OK;
+}
+
+int slg_filter(const int32_t *in_i, const int32_t *in_j, const int32_t *in_w, int64_t n,
+               int32_t s, int32_t *out_i, int32_t *out_j, int32_t *out_w, int64_t capacity,
+               int64_t *n_pairs, void *stream) {
+  if (!n_pairs || n < 0 || s < 1 || capacity < 0) return SLG_ERR_INVALID;
+  if (n > 0 && (!in_i || !in_j || !in_w)) return SLG_ERR_INVALID;
+  if (capacity > 0 && (!out_i || !out_j)) return SLG_ERR_INVALID;
+  *n_pairs = 0;
+  if (n == 0) return SLG_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  Pool pool(st);
+  long long *tile = nullptr;
+  const int64_t nt = keep_tiles(n);
+  SLG_TRY(pool.get(&tile, (size_t)nt + 1));
+  SLG_TRY(launch_keep_count(in_w, n, s, tile, st));
+  long long total = 0;
+  SLG_TRY(cudaMemcpyAsync(&total, tile + nt, sizeof(long long), cudaMemcpyDeviceToHost, st));
+  SLG_TRY(cudaStreamSynchronize(st));
+  *n_pairs = total;
+  if (total > capacity) return SLG_ERR_CAPACITY;
+  if (total > 0) SLG_TRY(launch_keep_write(in_i, in_j, in_w, n, s, tile, out_i, out_j, out_w, st));
+  SLG_TRY(cudaStreamSynchronize(st));
+  return SLG_OK;
+}
+
+int slg_build_sweep(const slg_hypergraph *h, const int32_t *s, int32_t count, uint32_t flags,
+                    int32_t *const *out_i, int32_t *const *out_j, int32_t *const *out_w,
+                    const int64_t *capacity, int64_t *n_pairs, void *stream) {
+  if (!h || !s || count < 1 || count > 64 || !out_i || !out_j || !out_w || !capacity ||
+      !n_pairs)
+    return SLG_ERR_INVALID;
+  if (flags & SLG_UNWEIGHTED) return SLG_ERR_UNSUPPORTED;  // the weights decide membership
+  int32_t k0 = 0;
+  for (int32_t k = 0; k < count; ++k) {
+    if (s[k] < 1) return SLG_ERR_INVALID;
+    n_pairs[k] = -1;
+    if (s[k] < s[k0]) k0 = k;
+  }
+  // L_{s_min} by one walk, into the caller's list of the smallest threshold
+  if (capacity[k0] > 0 && !out_w[k0]) return SLG_ERR_INVALID;
+  int rc = slg_build(h, s[k0], flags, out_i[k0], out_j[k0], out_w[k0], capacity[k0],
+                     &n_pairs[k0], stream);
+  if (rc != SLG_OK) return rc;
+  const slg_stats base_stats = t_stats;
+  const int64_t n0 = n_pairs[k0];
+  cudaStream_t st = (cudaStream_t)stream;
+  int result = SLG_OK;
+  for (int32_t k = 0; k < count; ++k) {
+    if (k == k0) continue;
+    if (s[k] == s[k0]) {  // the same list
+      n_pairs[k] = n0;
+      if (n0 > capacity[k]) {
+        result = SLG_ERR_CAPACITY;
+        continue;
+      }
+      if (n0 > 0) {
+        if (!out_i[k] || !out_j[k]) return SLG_ERR_INVALID;
+        SLG_TRY(cudaMemcpyAsync(out_i[k], out_i[k0], (size_t)n0 * 4, cudaMemcpyDeviceToDevice, st));
+        SLG_TRY(cudaMemcpyAsync(out_j[k], out_j[k0], (size_t)n0 * 4, cudaMemcpyDeviceToDevice, st));
+        if (out_w[k])
+          SLG_TRY(cudaMemcpyAsync(out_w[k], out_w[k0], (size_t)n0 * 4, cudaMemcpyDeviceToDevice,
+                                  st));
+      }
+      continue;
+    }
+    rc = slg_filter(out_i[k0], out_j[k0], out_w[k0], n0, s[k], out_i[k], out_j[k], out_w[k],
+                    capacity[k], &n_pairs[k], stream);
+    if (rc == SLG_ERR_CAPACITY) result = rc;
+    else if (rc != SLG_OK) return rc;
+  }
+  SLG_TRY(cudaStreamSynchronize(st));
+  t_stats = base_stats;
+  return result;
 }
 
 int slg_tile_overlap(const uint8_t *A, int32_t rows_pad, int32_t cols_pad, int32_t *C,

@@ -400,6 +400,16 @@ cudaError_t launch_unrelabel(int64_t P, int32_t R, const int32_t *perm, int32_t 
                              int32_t *out_j, int32_t *out_w, unsigned long long *keys,
                              int32_t *vals, int32_t *hist, cudaStream_t st, int32_t *launches);
 
+// Threshold filter of a canonical edge list (slg_sweep.cu): tile counts of
+// the triples with w >= s and their exclusive scan in `tile` (keep_tiles(n)
+// + 1 entries, tile[keep_tiles(n)] = total), then the ordered compaction.
+int64_t keep_tiles(int64_t n);
+cudaError_t launch_keep_count(const int32_t *w, int64_t n, int32_t s, long long *tile,
+                              cudaStream_t st);
+cudaError_t launch_keep_write(const int32_t *in_i, const int32_t *in_j, const int32_t *in_w,
+                              int64_t n, int32_t s, const long long *tile, int32_t *out_i,
+                              int32_t *out_j, int32_t *out_w, cudaStream_t st);
+
 // Filtered SpGEMM comparison: full-column tails / per-row work, filtration.
 cudaError_t launch_rows_full(const Side &sd, int32_t row_begin, int32_t row_end,
                              int32_t list_base, int32_t *tail_beg, int32_t *tail_end,
