@@ -528,23 +528,27 @@ def run_serve(args):
     gaps = rng.exponential(1.0 / args.rate, size=n)
     qs_spec = [(int(rng.integers(0, 16)), int(rng.integers(1, 65)), bool(rng.integers(0, 2)))
                for _ in range(n)]
-    srv = Server(dhs, slots=4, memory_budget=96 << 30)
-    t0 = time.perf_counter()
-    due = t0
-    queries = []
-    for gap, spec in zip(gaps, qs_spec):
-        due += gap
-        now = time.perf_counter()
-        if due > now:
-            time.sleep(due - now)
-        queries.append(srv.submit(*spec))
-    for q in queries:
-        q.wait()
-    wall = time.perf_counter() - t0
-    srv.close()
-    summ = Server.summary(queries, wall)
-    # the same queries one at a time through the plain kernel (first 100)
-    k = min(100, n)
+    runs = {}
+    for reuse in (False, True):
+        srv = Server(dhs, slots=4, memory_budget=96 << 30, reuse=reuse, cache_bytes=48 << 30)
+        t0 = time.perf_counter()
+        due = t0
+        queries = []
+        for gap, spec in zip(gaps, qs_spec):
+            due += gap
+            now = time.perf_counter()
+            if due > now:
+                time.sleep(due - now)
+            queries.append(srv.submit(*spec))
+        for q in queries:
+            q.wait()
+        wall = time.perf_counter() - t0
+        srv.close()
+        runs["reuse" if reuse else "walk_every_query"] = Server.summary(queries, wall)
+        del srv, queries
+        torch.cuda.empty_cache()
+    # the same queries one at a time through the plain kernel (first 40)
+    k = min(40, n)
     lat = []
     for gid, s, dual in qs_spec[:k]:
         torch.cuda.synchronize()
@@ -554,7 +558,7 @@ def run_serve(args):
         lat.append((time.perf_counter() - t) * 1e3)
     lat = np.array(lat)
     out = {"mode": "serve", "metric": "s-line-graph queries: latency and throughput",
-           "rate_per_s": args.rate, "slots": 4, **summ,
+           "rate_per_s": args.rate, "slots": 4, **runs,
            "plain_one_at_a_time": {"queries": k, "p50_ms": float(np.percentile(lat, 50)),
                                    "p99_ms": float(np.percentile(lat, 99)),
                                    "queries_per_s": k / (lat.sum() / 1e3)}}

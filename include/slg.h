@@ -216,6 +216,47 @@ int slg_build_sweep(const slg_hypergraph *h, const int32_t *s, int32_t count,
                     const int64_t *capacity, int64_t *n_pairs, void *stream);
 
 /*
+ * After the edge list.  Inputs are device pair lists (i < j, ids in [0, R));
+ * outputs are caller-owned device arrays.  Each call checks its input on
+ * the device first (SLG_ERR_INVALID for an id out of range, i >= j, or --
+ * where a canonical list is required -- pairs not strictly ascending) and
+ * synchronises `stream` before it returns.
+ *
+ * slg_squeeze -- ID squeezing (Section IV-E): the ids that occur in the
+ *   list are renumbered 0 .. n_ids-1 in ascending order of their original
+ *   id (a canonical list stays canonical).
+ *     out_i, out_j  [n] the list in new ids (may not overlap the input)
+ *     old_of_new    [R] receives the original id of every new id (first
+ *                   n_ids entries)
+ *     n_ids         host pointer, receives the number of distinct ids
+ *
+ * slg_adjacency -- the adjacency of the line graph: symmetric CSR with V
+ *   vertices built from a CANONICAL list (for instance a squeezed one, with
+ *   V = n_ids).  Row v holds its neighbours in ascending order.
+ *     adj_off  [V + 1] device int64 offsets
+ *     adj      [2 n] neighbour ids; adj_w [2 n] their weights, or NULL
+ *     in_w     required when adj_w is given
+ *   n < 2^30.
+ *
+ * slg_components -- s-connected components: the connected components of
+ *   L_s (Section I lists them as the analysis the s-line graph serves).
+ *     labels        [R] receives for every id the smallest id of its
+ *                   component (its own id when it occurs in no pair)
+ *     n_components  host pointer, receives the number of components among
+ *                   the ids that occur in the list
+ *   R <= 2^24.  SLG_ERR_TIMEOUT if a bounded device loop gave up.
+ */
+int slg_squeeze(const int32_t *in_i, const int32_t *in_j, int64_t n, int32_t R,
+                int32_t *out_i, int32_t *out_j, int32_t *old_of_new,
+                int32_t *n_ids, void *stream);
+int slg_adjacency(const int32_t *in_i, const int32_t *in_j, const int32_t *in_w,
+                  int64_t n, int32_t V, int64_t *adj_off, int32_t *adj,
+                  int32_t *adj_w, void *stream);
+int slg_components(const int32_t *in_i, const int32_t *in_j, int64_t n,
+                   int32_t R, int32_t *labels, int64_t *n_components,
+                   void *stream);
+
+/*
  * slg_tile_overlap -- exact overlap counts of a dense 0/1 block on the
  * tensor cores: C = A·Aᵀ, the linear-algebra form of Section IV-D applied to
  * a dense core of the incidence (the dense-core tile path).

@@ -24,6 +24,15 @@ Three independent ways to compute the same set:
 ``wedges`` gives the exact work of the s-filtered walk in closed form,
 sum over vertices of C(d_s(v), 2) with d_s(v) the number of hyperedges of
 size >= s containing v.
+
+After the edge list, by their plain definitions:
+
+* ``squeeze``     -- ID squeezing (Section IV-E): the ids occurring in the
+                     list, renumbered in ascending order;
+* ``adjacency``   -- the symmetric CSR of L_s, rows ascending;
+* ``components``  -- connected components of L_s (s-connected components,
+                     Section I), each id labelled by the smallest id of its
+                     component; scipy's graph search is the library step.
 """
 from __future__ import annotations
 
@@ -193,3 +202,47 @@ def canonical(i, j, w):
     """Stack triples into one int64 array of shape (P, 3) for comparisons."""
     return np.stack([np.asarray(i, np.int64), np.asarray(j, np.int64),
                      np.asarray(w, np.int64)], axis=1)
+
+
+def squeeze(i, j, R: int):
+    """(i', j', old_of_new): the ids of the list renumbered 0 .. k-1 in
+    ascending order of their original id (Section IV-E)."""
+    i = np.asarray(i, np.int64)
+    j = np.asarray(j, np.int64)
+    ids = np.unique(np.concatenate([i, j]))
+    return (np.searchsorted(ids, i).astype(np.int32), np.searchsorted(ids, j).astype(np.int32),
+            ids.astype(np.int32))
+
+
+def adjacency(i, j, w, V: int):
+    """Symmetric CSR of the line graph: (off [V+1] int64, adj, adj_w), every
+    pair listed in the rows of both its ends, each row ascending."""
+    i = np.asarray(i, np.int64)
+    j = np.asarray(j, np.int64)
+    w = np.asarray(w, np.int64)
+    rows = np.concatenate([i, j])
+    cols = np.concatenate([j, i])
+    ws = np.concatenate([w, w])
+    order = np.lexsort((cols, rows))
+    off = np.zeros(V + 1, np.int64)
+    off[1:] = np.cumsum(np.bincount(rows, minlength=V))
+    return off, cols[order].astype(np.int32), ws[order].astype(np.int32)
+
+
+def components(i, j, R: int):
+    """(labels [R], count): for every id the smallest id of its connected
+    component in the graph with edges (i, j) (its own id when isolated), and
+    the number of components among the ids that occur in an edge."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+    i = np.asarray(i, np.int64)
+    j = np.asarray(j, np.int64)
+    g = coo_matrix((np.ones(len(i), np.int8), (i, j)), shape=(R, R))
+    _, lab = connected_components(g, directed=False)
+    smallest = np.full(lab.max() + 1 if R else 0, R, np.int64)
+    np.minimum.at(smallest, lab, np.arange(R))
+    labels = smallest[lab].astype(np.int32)
+    used = np.zeros(R, bool)
+    used[i] = True
+    used[j] = True
+    return labels, int(np.unique(labels[used]).size)

@@ -21,7 +21,7 @@ import numpy as np
 __all__ = [
     "DeviceHypergraph", "to_device", "count", "build", "build_rows",
     "build_host", "wedges", "last_stats", "set_profiling", "tile_overlap",
-    "filter_pairs", "build_sweep",
+    "filter_pairs", "build_sweep", "squeeze", "adjacency", "components",
     "set_core_params", "SLG_TENSOR_CORE", "SLG_RELABEL_ASC", "SLG_RELABEL_DESC",
     "SLG_NO_PRUNE",
     "Plan", "alloc_outputs",
@@ -111,6 +111,12 @@ ABI_FUNCTIONS = {
                                   _VP, ctypes.c_int64, _I64P, _VP]),
     "slg_build_sweep": (ctypes.c_int, [_HP, _VP, ctypes.c_int32, ctypes.c_uint32, _VP, _VP,
                                        _VP, _VP, _VP, _VP]),
+    "slg_squeeze": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, ctypes.c_int32, _VP, _VP, _VP,
+                                   ctypes.POINTER(ctypes.c_int32), _VP]),
+    "slg_adjacency": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int32, _VP, _VP,
+                                     _VP, _VP]),
+    "slg_components": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, ctypes.c_int32, _VP, _I64P,
+                                      _VP]),
     "slg_plan_create": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, ctypes.c_uint32,
                                        ctypes.POINTER(ctypes.c_void_p), _VP]),
     "slg_plan_execute": (ctypes.c_int, [_VP, _VP]),
@@ -374,6 +380,56 @@ def build_sweep(h: DeviceHypergraph, s_list, dual=False, algo="binned", outs=Non
     for (a, b, c), p in zip(outs, list(np_)):
         res.append((a[:p], b[:p], c[:p] if c is not None else None))
     return res
+
+
+def _ptr(t):
+    return t.data_ptr() if t is not None and t.numel() else None
+
+
+def squeeze(i, j, R: int, stream=None):
+    """ID squeezing: (i', j', old_of_new) with the ids of the list renumbered
+    0 .. n_ids-1 in ascending order of their original id."""
+    import torch
+    n = int(i.shape[0])
+    oi = torch.empty(max(n, 1), dtype=torch.int32, device=i.device)
+    oj = torch.empty(max(n, 1), dtype=torch.int32, device=i.device)
+    old = torch.empty(max(int(R), 1), dtype=torch.int32, device=i.device)
+    k = ctypes.c_int32(0)
+    rc = load().slg_squeeze(_ptr(i), _ptr(j), n, int(R), oi.data_ptr(), oj.data_ptr(),
+                            old.data_ptr(), ctypes.byref(k), _stream(stream))
+    if rc != 0:
+        raise SlgError(rc, "slg_squeeze")
+    return oi[:n], oj[:n], old[:k.value]
+
+
+def adjacency(i, j, w, V: int, weights=True, stream=None):
+    """Symmetric CSR (off int64 [V+1], adj int32 [2n], adj_w or None) of the
+    line graph from a canonical list over V vertices."""
+    import torch
+    n = int(i.shape[0])
+    off = torch.empty(int(V) + 1, dtype=torch.int64, device=i.device)
+    adj = torch.empty(max(2 * n, 1), dtype=torch.int32, device=i.device)
+    adj_w = torch.empty(max(2 * n, 1), dtype=torch.int32, device=i.device) if weights else None
+    rc = load().slg_adjacency(_ptr(i), _ptr(j), _ptr(w) if weights else None, n, int(V),
+                              off.data_ptr(), adj.data_ptr(),
+                              adj_w.data_ptr() if weights else None, _stream(stream))
+    if rc != 0:
+        raise SlgError(rc, "slg_adjacency")
+    return off, adj[:2 * n], (adj_w[:2 * n] if weights else None)
+
+
+def components(i, j, R: int, stream=None):
+    """(labels [R], n_components): the smallest id of each id's component in
+    L_s, and the number of components among the ids of the list."""
+    import torch
+    n = int(i.shape[0])
+    labels = torch.empty(max(int(R), 1), dtype=torch.int32, device=i.device)
+    k = ctypes.c_int64(0)
+    rc = load().slg_components(_ptr(i), _ptr(j), n, int(R), labels.data_ptr(),
+                               ctypes.byref(k), _stream(stream))
+    if rc != 0:
+        raise SlgError(rc, "slg_components")
+    return labels[:int(R)], int(k.value)
 
 
 def last_stats() -> dict:

@@ -999,6 +999,107 @@ int slg_build_sweep(const slg_hypergraph *h, const int32_t *s, int32_t count, ui
   return result;
 }
 
+// Device check of a pair list; returns SLG_OK or SLG_ERR_INVALID (synchronises).
+static int check_pairs(const int32_t *a, const int32_t *b, int64_t n, int32_t R, int canonical,
+                       Pool &pool, cudaStream_t st) {
+  if (n == 0) return SLG_OK;
+  int32_t *err = nullptr;
+  SLG_TRY(pool.get(&err, 1));
+  SLG_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
+  SLG_TRY(launch_check_pairs(a, b, n, R, canonical, err, st));
+  int32_t h = 0;
+  SLG_TRY(cudaMemcpyAsync(&h, err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  SLG_TRY(cudaStreamSynchronize(st));
+  return h ? SLG_ERR_INVALID : SLG_OK;
+}
+
+int slg_squeeze(const int32_t *in_i, const int32_t *in_j, int64_t n, int32_t R, int32_t *out_i,
+                int32_t *out_j, int32_t *old_of_new, int32_t *n_ids, void *stream) {
+  if (!n_ids || n < 0 || R < 0 || (n > 0 && (!in_i || !in_j || !out_i || !out_j)) ||
+      (R > 0 && !old_of_new))
+    return SLG_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  Pool pool(st);
+  int rc = check_pairs(in_i, in_j, n, R, 0, pool, st);
+  if (rc) return rc;
+  int32_t *mark, *rank, *tile;
+  SLG_TRY(pool.get(&mark, (size_t)R + 1));
+  SLG_TRY(pool.get(&rank, (size_t)R + 1));
+  SLG_TRY(pool.get(&tile, (size_t)xscan_tiles((int64_t)R + 1) + 1));
+  SLG_TRY(cudaMemsetAsync(mark, 0, ((size_t)R + 1) * sizeof(int32_t), st));
+  SLG_TRY(launch_mark(in_i, in_j, n, mark, st));
+  SLG_TRY(launch_xscan(mark, rank, (int64_t)R + 1, tile, st));
+  SLG_TRY(launch_squeeze(in_i, in_j, n, R, mark, rank, out_i, out_j, old_of_new, st));
+  int32_t ids = 0;
+  SLG_TRY(cudaMemcpyAsync(&ids, rank + R, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  SLG_TRY(cudaStreamSynchronize(st));
+  *n_ids = ids;
+  return SLG_OK;
+}
+
+int slg_adjacency(const int32_t *in_i, const int32_t *in_j, const int32_t *in_w, int64_t n,
+                  int32_t V, int64_t *adj_off, int32_t *adj, int32_t *adj_w, void *stream) {
+  if (n < 0 || V < 0 || n >= ((int64_t)1 << 30) || !adj_off ||
+      (n > 0 && (!in_i || !in_j || !adj || (adj_w && !in_w))))
+    return SLG_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  Pool pool(st);
+  int rc = check_pairs(in_i, in_j, n, V, 1, pool, st);
+  if (rc) return rc;
+  int32_t *up, *lo;
+  SLG_TRY(pool.get(&up, (size_t)V + 1));
+  SLG_TRY(pool.get(&lo, (size_t)V + 1));
+  SLG_TRY(cudaMemsetAsync(up, 0, ((size_t)V + 1) * sizeof(int32_t), st));
+  SLG_TRY(cudaMemsetAsync(lo, 0, ((size_t)V + 1) * sizeof(int32_t), st));
+  long long *off = reinterpret_cast<long long *>(adj_off);
+  SLG_TRY(launch_adjacency_offsets(in_i, in_j, n, V, up, lo, off, st));
+  if (n > 0) {
+    long long *first, *lfirst;
+    uint32_t *keys, *keys_tmp;
+    int32_t *pos, *pos_tmp, *hist;
+    SLG_TRY(pool.get(&first, (size_t)V + 1));
+    SLG_TRY(pool.get(&lfirst, (size_t)V + 1));
+    SLG_TRY(pool.get(&keys, (size_t)n));
+    SLG_TRY(pool.get(&keys_tmp, (size_t)n));
+    SLG_TRY(pool.get(&pos, (size_t)n));
+    SLG_TRY(pool.get(&pos_tmp, (size_t)n));
+    SLG_TRY(pool.get(&hist, radix_sort_scratch_ints(n)));
+    SLG_TRY(launch_adjacency_fill(in_i, in_j, in_w, n, V, off, lo, first, lfirst, keys,
+                                  keys_tmp, pos, pos_tmp, hist, adj, adj_w, st));
+  }
+  SLG_TRY(cudaStreamSynchronize(st));
+  return SLG_OK;
+}
+
+int slg_components(const int32_t *in_i, const int32_t *in_j, int64_t n, int32_t R,
+                   int32_t *labels, int64_t *n_components, void *stream) {
+  if (!n_components || n < 0 || R < 0 || R > kGiantMaxR || (n > 0 && (!in_i || !in_j)) ||
+      (R > 0 && !labels))
+    return SLG_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  Pool pool(st);
+  int rc = check_pairs(in_i, in_j, n, R, 0, pool, st);
+  if (rc) return rc;
+  int32_t *mark, *err;
+  unsigned long long *cnt;
+  SLG_TRY(pool.get(&mark, (size_t)R + 1));
+  SLG_TRY(pool.get(&err, 1));
+  SLG_TRY(pool.get(&cnt, 1));
+  SLG_TRY(cudaMemsetAsync(mark, 0, ((size_t)R + 1) * sizeof(int32_t), st));
+  SLG_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
+  SLG_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
+  SLG_TRY(launch_mark(in_i, in_j, n, mark, st));
+  SLG_TRY(launch_components(in_i, in_j, n, R, labels, mark, cnt, err, st));
+  unsigned long long hc = 0;
+  int32_t he = 0;
+  SLG_TRY(cudaMemcpyAsync(&hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
+  SLG_TRY(cudaMemcpyAsync(&he, err, sizeof(he), cudaMemcpyDeviceToHost, st));
+  SLG_TRY(cudaStreamSynchronize(st));
+  if (he) return SLG_ERR_TIMEOUT;  // a bounded loop gave up (not expected)
+  *n_components = (int64_t)hc;
+  return SLG_OK;
+}
+
 int slg_tile_overlap(const uint8_t *A, int32_t rows_pad, int32_t cols_pad, int32_t *C,
                      void *stream) {
   if (!A || !C || rows_pad <= 0 || cols_pad <= 0 || rows_pad % 128 || cols_pad % 128 ||

@@ -410,6 +410,26 @@ cudaError_t launch_keep_write(const int32_t *in_i, const int32_t *in_j, const in
                               int64_t n, int32_t s, const long long *tile, int32_t *out_i,
                               int32_t *out_j, int32_t *out_w, cudaStream_t st);
 
+// After the edge list (slg_post.cu): pair checks, ID squeezing, adjacency,
+// components.
+cudaError_t launch_check_pairs(const int32_t *a, const int32_t *b, int64_t n, int32_t R,
+                               int canonical, int32_t *err, cudaStream_t st);
+cudaError_t launch_mark(const int32_t *a, const int32_t *b, int64_t n, int32_t *mark,
+                        cudaStream_t st);
+cudaError_t launch_squeeze(const int32_t *a, const int32_t *b, int64_t n, int32_t R,
+                           const int32_t *mark, const int32_t *rank, int32_t *oa, int32_t *ob,
+                           int32_t *old_of_new, cudaStream_t st);
+cudaError_t launch_adjacency_offsets(const int32_t *a, const int32_t *b, int64_t n, int32_t V,
+                                     int32_t *up, int32_t *lo, long long *off, cudaStream_t st);
+cudaError_t launch_adjacency_fill(const int32_t *a, const int32_t *b, const int32_t *w,
+                                  int64_t n, int32_t V, const long long *off, const int32_t *lo,
+                                  long long *first, long long *lfirst, uint32_t *keys,
+                                  uint32_t *keys_tmp, int32_t *pos, int32_t *pos_tmp,
+                                  int32_t *hist, int32_t *adj, int32_t *adj_w, cudaStream_t st);
+cudaError_t launch_components(const int32_t *a, const int32_t *b, int64_t n, int32_t R,
+                              int32_t *labels, const int32_t *mark, unsigned long long *n_comp,
+                              int32_t *err, cudaStream_t st);
+
 // Filtered SpGEMM comparison: full-column tails / per-row work, filtration.
 cudaError_t launch_rows_full(const Side &sd, int32_t row_begin, int32_t row_end,
                              int32_t list_base, int32_t *tail_beg, int32_t *tail_end,

@@ -236,8 +236,78 @@ def pin_rows_subset(lib_path=None):
     return fails
 
 
+def _bfs_labels(R, pairs):
+    """Smallest id of each id's component by breadth-first search."""
+    nb = {v: [] for v in range(R)}
+    for a, b in pairs:
+        nb[a].append(b)
+        nb[b].append(a)
+    lab = [-1] * R
+    for v in range(R):
+        if lab[v] < 0:
+            comp, todo = [v], [v]
+            lab[v] = v
+            while todo:
+                x = todo.pop()
+                for y in nb[x]:
+                    if lab[y] < 0:
+                        lab[y] = v
+                        comp.append(y)
+                        todo.append(y)
+    return lab  # v is the smallest id of its component when first reached
+
+
+def pin_post(lib_path=None):
+    """Squeezing, adjacency and components of L_s against their definitions:
+    Fig. 1 (L_1(H) = {AB, BC, BD, CD} is one component; L_2(H) = {AB, BC}
+    leaves D out; L_3(H) = {BC}), a path, and breadth-first search / dict
+    construction on random small lists."""
+    fails = []
+    names, rows, _ = load_fig1()
+    h = hg.from_rows(rows, n=max(max(r) for r in rows) + 1)
+    want = {1: ([0] * 4, 1), 2: ([0, 0, 0, 3], 1), 3: ([0, 1, 1, 3], 1)}
+    for s, (lab, k) in want.items():
+        t = _lg(h, s, lib_path)
+        got, cnt = oracle.components(t[:, 0], t[:, 1], 4)
+        if list(got) != lab or cnt != k:
+            fails.append(f"Fig. 1 components at s={s}: {list(got)} / {cnt}")
+    # a path 0-1-...-9 plus an isolated id 10 and an edge 11-12
+    i = np.array(list(range(9)) + [11])
+    j = np.array(list(range(1, 10)) + [12])
+    got, cnt = oracle.components(i, j, 13)
+    if list(got) != [0] * 10 + [10, 11, 11] or cnt != 2:
+        fails.append(f"path components {list(got)} / {cnt}")
+    rng = np.random.default_rng(5)
+    for trial in range(40):
+        R = int(rng.integers(1, 40))
+        k = int(rng.integers(0, 60))
+        pairs = sorted({tuple(sorted(rng.choice(R, 2, replace=False))) for _ in range(k)}
+                       if R > 1 else set())
+        i = np.array([p[0] for p in pairs], np.int64)
+        j = np.array([p[1] for p in pairs], np.int64)
+        w = rng.integers(1, 9, len(pairs))
+        lab, cnt = oracle.components(i, j, R)
+        ref = _bfs_labels(R, pairs)
+        used = sorted({x for p in pairs for x in p})
+        if list(lab) != ref or cnt != len({ref[v] for v in used}):
+            fails.append(f"components trial {trial}")
+        si, sj, old = oracle.squeeze(i, j, R)
+        if list(old) != used or any(old[si[q]] != i[q] or old[sj[q]] != j[q]
+                                    for q in range(len(pairs))):
+            fails.append(f"squeeze trial {trial}")
+        off, adj, aw = oracle.adjacency(i, j, w, R)
+        for v in range(R):
+            want_row = sorted([(b, int(c)) for (a, b), c in zip(pairs, w) if a == v] +
+                              [(a, int(c)) for (a, b), c in zip(pairs, w) if b == v])
+            row = list(zip(adj[off[v]:off[v + 1]].tolist(), aw[off[v]:off[v + 1]].tolist()))
+            if row != want_row:
+                fails.append(f"adjacency trial {trial} row {v}")
+                break
+    return fails
+
+
 ALL_PINS = [pin_fig1, pin_brute_force, pin_closed_forms, pin_special_cases,
-            pin_invariants, pin_scipy, pin_rows_subset]
+            pin_invariants, pin_scipy, pin_rows_subset, pin_post]
 
 
 def run_all(lib_path=None):

@@ -65,3 +65,24 @@ def test_tiny_budget_admits_one_at_a_time(pool):
     for (a0, a1), (b0, b1) in zip(spans, spans[1:]):
         assert b0 >= a1 - 1e-6          # never two queries in flight
     assert all(q.error is None for q in qs)
+
+
+def test_reuse_filters_equal_walks(pool):
+    # with reuse, queries at larger thresholds are answered by filtering the
+    # kept list of a smaller one; every result must still equal a fresh build
+    from paper_2010_11448_gb300.serve import Server
+    hs, dhs = pool
+    reqs = [(g, s, d) for s in (1, 3, 2, 5, 8, 4) for g in (0, 2) for d in (False, True)]
+    srv = Server(dhs, slots=2, keep_results=True, reuse=True)
+    qs = []
+    for r in reqs:
+        q = srv.submit(*r)
+        assert q.wait(300)  # one after another: each finds the lists kept so far
+        qs.append(q)
+    srv.close()
+    for (gid, s, dual), q in zip(reqs, qs):
+        assert q.error is None
+        assert np.array_equal(as_np(q.result), as_np(slg.build(dhs[gid], s, dual=dual)))
+    # s = 1 is built first for every graph and side; all later ones filter
+    assert [q.reused for q in qs] == [False] * 4 + [True] * (len(reqs) - 4)
+    assert Server.summary(qs, 1.0)["answered_by_filter"] == len(reqs) - 4
