@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (testing)")
     ap.add_argument("--builds", default="all",
                     help="comma list of builds to run, e.g. 'H:8,H*:2' (profiling)")
-    ap.add_argument("--mode", choices=["headline", "batch", "serve", "core", "sweep", "ablation"],
+    ap.add_argument("--mode", choices=["headline", "batch", "serve", "core", "sweep", "ablation",
+                                       "post"],
                     default="headline",
                     help="headline: the Chung-Lu build (default); batch: many hypergraphs "
                          "in one captured pipeline vs sequential builds; serve: Poisson "
@@ -450,34 +451,49 @@ def _setup_gpu():
 
 def run_batch(args):
     """Batched form: `batch_count` Chung-Lu hypergraphs (m log-uniform in
-    [1e3, batch_max], n = 2m), each with its own s ~ U{2..32}: one captured
-    pipeline (graph replay) vs the same builds one call at a time (binned, and
-    the plain per-hyperedge kernel)."""
+    [1e3, batch_max], n = 2m), each with its own s ~ U{2..32}: captured
+    pipelines (one graph replay per plan of at most 2^24 rows) vs the same
+    builds one call at a time (binned, and the plain per-hyperedge kernel)."""
     import numpy as np
     torch, slg = _setup_gpu()
     import hypergen
     t0 = time.perf_counter()
-    members = hypergen.batch(args.batch_count, seed=100, m_lo=1000, m_hi=args.batch_max)
+    members = hypergen.batch(args.batch_count, seed=100, m_lo=1000, m_hi=args.batch_max,
+                             workers=min(16, os.cpu_count() or 1))
+    print(f"batch: generated in {time.perf_counter() - t0:.0f} s", file=sys.stderr, flush=True)
     gen_s = time.perf_counter() - t0
     dhs = [slg.to_device(h) for h, _ in members]
     ss = [s for _, s in members]
     W = sum(slg.wedges(d, s) for d, s in zip(dhs, ss))
+    # one plan per group of members whose union stays within the library's
+    # largest side (2^24 rows); each plan is one captured graph launch
+    groups, cur, rows = [], [], 0
+    for k, d in enumerate(dhs):
+        if cur and rows + d.m > (1 << 24):
+            groups.append(cur)
+            cur, rows = [], 0
+        cur.append(k)
+        rows += d.m
+    groups.append(cur)
     t0 = time.perf_counter()
-    plan = slg.Plan(dhs, ss)
+    plans = [slg.Plan([dhs[k] for k in g], [ss[k] for k in g]) for g in groups]
     plan_s = time.perf_counter() - t0
-    info = plan.info()
+    print(f"batch: {len(plans)} plans in {plan_s:.0f} s", file=sys.stderr, flush=True)
+    infos = [p.info() for p in plans]
     st = torch.cuda.current_stream()
     for _ in range(args.warmup):
-        plan.execute()
+        for p in plans:
+            p.execute()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
     for _ in range(args.steps):
-        plan.execute()
+        for p in plans:
+            p.execute()
     e1.record(st)
     torch.cuda.synchronize()
     batched_ms = e0.elapsed_time(e1) / args.steps
-    res = plan.results()
+    res = [r for p in plans for r in p.results()]
     pairs = sum(int(r[0].shape[0]) for r in res)
     # sequential builds, binned and plain (each call sizes its own output)
     caps = [slg.count(d, s) for d, s in zip(dhs, ss)]
@@ -493,6 +509,7 @@ def run_batch(args):
             slg.build(d, s, algo=algo, out=o)
         torch.cuda.synchronize()
         seq[algo] = (time.perf_counter() - t) * 1e3
+        print(f"batch: sequential {algo} {seq[algo]:.0f} ms", file=sys.stderr, flush=True)
     # the batched result equals the sequential one, member by member
     same = all(torch.equal(r[1], o[1][:c]) and torch.equal(r[2], o[2][:c])
                for r, o, c in zip(res, outs, caps))
@@ -503,8 +520,11 @@ def run_batch(args):
            "sequential_binned_ms": seq["binned"], "sequential_plain_ms": seq["plain"],
            "speedup_vs_plain": seq["plain"] / batched_ms,
            "speedup_vs_sequential_binned": seq["binned"] / batched_ms,
-           "bit_identical_to_sequential": bool(same), "autotuned_bins": info["bins"],
-           "kernels_per_launch": info["launches"], "plan_s": plan_s, "generate_s": gen_s,
+           "bit_identical_to_sequential": bool(same), "plans": len(plans),
+           "members_per_plan": [len(g) for g in groups],
+           "autotuned_bins": [i["bins"] for i in infos],
+           "kernels_per_launch": [i["launches"] for i in infos], "plan_s": plan_s,
+           "generate_s": gen_s,
            "steps": args.steps, "warmup": args.warmup}
     print(json.dumps(out), flush=True)
     return 0
@@ -547,6 +567,7 @@ def run_serve(args):
         runs["reuse" if reuse else "walk_every_query"] = Server.summary(queries, wall)
         del srv, queries
         torch.cuda.empty_cache()
+    torch.cuda.empty_cache()
     # the same queries one at a time through the plain kernel (first 40)
     k = min(40, n)
     lat = []
@@ -695,6 +716,45 @@ def run_ablation(args):
     return 0
 
 
+def run_post(args):
+    """After the edge list, on the headline workload: ID squeezing, the
+    symmetric adjacency of the squeezed list and the s-connected components,
+    for L_s at s = 2, 8 on H and H* (ms, best of 3)."""
+    torch, slg = _setup_gpu()
+    h = make_workload(0, args.scale)
+    dh = slg.to_device(h)
+    rows = {}
+
+    def best(fn):
+        b = None
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            r = fn()
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t) * 1e3
+            b = ms if b is None or ms < b else b
+        return b, r
+    for dual in (False, True):
+        R = h.n if dual else h.m
+        for s in (2, 8):
+            i, j, w = slg.build(dh, s, dual=dual)
+            t_sq, (si, sj, old) = best(lambda: slg.squeeze(i, j, R))
+            V = int(old.shape[0])
+            t_adj, _ = best(lambda: slg.adjacency(si, sj, w, V))
+            t_cc, (lab, k) = best(lambda: slg.components(i, j, R))
+            _, k2 = slg.components(si, sj, V)
+            rows[f"{'H*' if dual else 'H'} s={s}"] = {
+                "pairs": int(i.shape[0]), "ids": V, "components": k,
+                "components_squeezed_agree": k == k2, "squeeze_ms": t_sq,
+                "adjacency_ms": t_adj, "components_ms": t_cc}
+            del i, j, w, si, sj, old, lab
+    print(json.dumps({"mode": "post", "metric": "ID squeezing, adjacency, s-connected "
+                      "components after the build, ms", "workload": WORKLOAD_TEXT,
+                      "builds": rows}), flush=True)
+    return 0
+
+
 def main():
     global _ONLY
     args = parse()
@@ -715,6 +775,8 @@ def main():
         return run_sweep(args)
     if args.mode == "ablation":
         return run_ablation(args)
+    if args.mode == "post":
+        return run_post(args)
     return run_ours(args)
 
 

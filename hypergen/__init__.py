@@ -247,20 +247,29 @@ def lognormal_web(m: int, n: int, seed: int, mu: float = 2.0,
     return from_pairs(r, c, m, n, name)
 
 
+def _batch_member(args):
+    mk, seed, k = args
+    return chung_lu(mk, 2 * mk, seed, name=f"batch{k}")
+
+
 def batch(count: int, seed: int, m_lo: int = 1_000, m_hi: int = 200_000,
-          s_lo: int = 2, s_hi: int = 32):
+          s_lo: int = 2, s_hi: int = 32, workers: int = 1):
     """``count`` Chung-Lu hypergraphs with m log-uniform in [m_lo, m_hi],
     n = 2m, mean size 20, each with its own s ~ U{s_lo..s_hi}.  Graph k uses
-    seed ``seed + k``.  Returns a list of (Hypergraph, s)."""
+    seed ``seed + k``, so the result does not depend on ``workers`` (spawned
+    processes generating members in parallel).  Returns a list of
+    (Hypergraph, s)."""
     rng = np.random.default_rng(seed)
     ms = np.exp(rng.uniform(np.log(m_lo), np.log(m_hi), size=count))
     ss = rng.integers(s_lo, s_hi + 1, size=count)
-    out = []
-    for k in range(count):
-        mk = int(ms[k])
-        h = chung_lu(mk, 2 * mk, seed + k, name=f"batch{k}")
-        out.append((h, int(ss[k])))
-    return out
+    jobs = [(int(ms[k]), seed + k, k) for k in range(count)]
+    if workers > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            hs = pool.map(_batch_member, jobs, chunksize=1)
+    else:
+        hs = [_batch_member(j) for j in jobs]
+    return [(h, int(ss[k])) for k, h in enumerate(hs)]
 
 
 def random_small(seed: int, m_max: int = 24, n_max: int = 24,

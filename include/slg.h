@@ -400,6 +400,13 @@ const char *slg_strerror(int status);
 /* SLG_ABI_VERSION of the loaded library. */
 int slg_abi_version(void);
 
+/* Which device-side check raised the last error reported to this host
+ * thread: 0 none, 1 row offsets, 2 row ids (range or order), 3 column
+ * offsets, 4 column ids, 5 CSR and CSC differ, 6 a hash table or survivor
+ * list exceeded its bound, 7 a giant-row scratch bound, 8 staged pairs
+ * without staging room (a build that produced more pairs than counted). */
+int slg_last_error_where(void);
+
 #ifdef __cplusplus
 }
 #endif

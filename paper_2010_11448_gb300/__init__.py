@@ -55,7 +55,9 @@ def library_path() -> str:
 class SlgError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
-        super().__init__(f"{what}: {_strerror(status)} (status {status})")
+        self.where = _last_where() if status == 1 else 0
+        at = f", device check {self.where}" if self.where else ""
+        super().__init__(f"{what}: {_strerror(status)} (status {status}{at})")
 
 
 class _Hypergraph(ctypes.Structure):
@@ -128,6 +130,7 @@ ABI_FUNCTIONS = {
     "slg_plan_destroy": (ctypes.c_int, [_VP]),
     "slg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "slg_abi_version": (ctypes.c_int, []),
+    "slg_last_error_where": (ctypes.c_int, []),
 }
 
 _lib = None
@@ -153,6 +156,13 @@ def load(path: str | None = None):
         if path is None:
             _lib = lib
         return lib
+
+
+def _last_where() -> int:
+    try:
+        return int(load().slg_last_error_where())
+    except Exception:  # pragma: no cover - library missing
+        return 0
 
 
 def _strerror(status: int) -> str:

@@ -3,6 +3,8 @@
 // kernels, and the single device->host read of the pair count.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <memory>
 #include <mutex>
 #include <vector>
@@ -65,6 +67,19 @@ int status_of(cudaError_t e) {
   return SLG_ERR_CUDA;
 }
 
+// The library's freed stream-ordered memory stays in the device's pool for
+// the next call (release threshold: unlimited).  When an allocation fails,
+// the pool's unused memory goes back to the driver and the allocation is
+// tried once more, so that memory the pool keeps never starves an
+// allocation (the pool's own, or a plain cudaMalloc).
+void trim_pool() {
+  int dev = 0;
+  cudaMemPool_t pool;
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess)
+    cudaMemPoolTrimTo(pool, 0);
+  cudaGetLastError();
+}
+
 // Stream-ordered allocations released (stream-ordered) when the call ends.
 struct Pool {
   cudaStream_t st;
@@ -76,6 +91,12 @@ struct Pool {
     if (bytes < 16) bytes = 16;
     void *q = nullptr;
     cudaError_t e = cudaMallocAsync(&q, bytes, st);
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      cudaStreamSynchronize(st);  // frees queued on the stream complete first
+      trim_pool();
+      e = cudaMallocAsync(&q, bytes, st);
+    }
     if (e != cudaSuccess) {
       cudaGetLastError();
       *p = nullptr;
@@ -90,13 +111,26 @@ struct Pool {
   }
 };
 
-#define SLG_TRY(expr)                         \
-  do {                                        \
-    cudaError_t _e = (expr);                  \
-    if (_e != cudaSuccess) {                  \
-      cudaGetLastError();                     \
-      return status_of(_e);                   \
-    }                                         \
+// With the environment variable SLG_DEBUG set, every failing CUDA step is
+// reported on stderr with its source expression (host side only).
+bool debug_on() {
+  static const bool on = std::getenv("SLG_DEBUG") != nullptr;
+  return on;
+}
+
+cudaError_t debug_fail(cudaError_t e, const char *what, int line) {
+  if (e != cudaSuccess && debug_on())
+    std::fprintf(stderr, "slg: line %d: %s: %s\n", line, what, cudaGetErrorString(e));
+  return e;
+}
+
+#define SLG_TRY(expr)                                          \
+  do {                                                         \
+    cudaError_t _e = debug_fail((expr), #expr, __LINE__);      \
+    if (_e != cudaSuccess) {                                   \
+      cudaGetLastError();                                      \
+      return status_of(_e);                                    \
+    }                                                          \
   } while (0)
 
 int check_args(const slg_hypergraph *h, int32_t s, uint32_t flags) {
@@ -166,7 +200,16 @@ cudaError_t ensure_giant(DeviceCtx &c, size_t elems, cudaStream_t st) {
   c.giant = nullptr;
   c.giant_elems = 0;
   e = cudaMalloc(&c.giant, elems * sizeof(int32_t));
-  if (e != cudaSuccess) return e;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    trim_pool();
+    e = cudaMalloc(&c.giant, elems * sizeof(int32_t));
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c.giant = nullptr;
+    return e;
+  }
   e = cudaMemset(c.giant, 0, elems * sizeof(int32_t));
   if (e != cudaSuccess) return e;
   c.giant_elems = elems;
@@ -239,9 +282,12 @@ cudaError_t giant_scratch(Call &c, int32_t max_work, WalkLaunch *L) {
   return e;
 }
 
+thread_local int32_t t_err_where = 0;  // kWhere* of the last device-raised error
+
 int read_meta(Call &c) {
   SLG_TRY(cudaMemcpyAsync(c.meta_host, c.w.meta, sizeof(Meta), cudaMemcpyDeviceToHost, c.st));
   SLG_TRY(cudaStreamSynchronize(c.st));
+  if (c.meta_host->err) t_err_where = c.meta_host->err_where;
   return c.meta_host->err;
 }
 
@@ -421,7 +467,7 @@ int run_binned(Call &c, int64_t *result) {
   if (pairs > 0) {
     if (m.stage_overflow == 0) {
       SLG_TRY(launch_gather(c.row_begin, c.rows, w, c.out_i, c.out_j, c.out_w, c.unweighted,
-                            c.st));
+                            c.capacity, c.st));
       c.launches += 1;
     } else {
       // Staging too small: walk again, writing straight to the output.
@@ -745,6 +791,11 @@ struct Owned {
     if (bytes < 16) bytes = 16;
     void *q = nullptr;
     cudaError_t e = cudaMalloc(&q, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      trim_pool();
+      e = cudaMalloc(&q, bytes);
+    }
     if (e != cudaSuccess) {
       cudaGetLastError();
       *p = nullptr;
@@ -788,15 +839,20 @@ namespace slg {
 namespace {
 
 // The whole build of a plan, enqueued without any host synchronisation.
+#define PLAN_TRY(expr)                                          \
+  do {                                                          \
+    const cudaError_t _e = debug_fail((expr), #expr, __LINE__); \
+    if (_e != cudaSuccess) return _e;                           \
+  } while (0)
+
 cudaError_t enqueue_plan(slg_plan *p, const Bins &bins, cudaStream_t st, int32_t *launches) {
   Work &w = p->w;
   const Side &sd = p->sd;
-  cudaError_t e = cudaMemsetAsync(w.meta, 0, sizeof(Meta), st);
-  if (e != cudaSuccess) return e;
-  if ((e = launch_validate(sd, w.meta, st)) != cudaSuccess) return e;
-  if ((e = launch_csr2csc(sd, w.csr2csc, w.meta, st)) != cudaSuccess) return e;
-  if ((e = launch_filter(sd, 1, w, st)) != cudaSuccess) return e;
-  if ((e = launch_rows_work(sd, 1, 0, sd.R, w, CoreInfo{}, bins, st)) != cudaSuccess) return e;
+  PLAN_TRY(cudaMemsetAsync(w.meta, 0, sizeof(Meta), st));
+  PLAN_TRY(launch_validate(sd, w.meta, st));
+  PLAN_TRY(launch_csr2csc(sd, w.csr2csc, w.meta, st));
+  PLAN_TRY(launch_filter(sd, 1, w, st));
+  PLAN_TRY(launch_rows_work(sd, 1, 0, sd.R, w, CoreInfo{}, bins, st));
   WalkLaunch L = {};
   L.w.r_off = sd.r_off;
   L.w.r_idx = sd.r_idx;
@@ -822,23 +878,20 @@ cudaError_t enqueue_plan(slg_plan *p, const Bins &bins, cudaStream_t st, int32_t
   L.giant_scratch = p->giant;
   L.giant_stride = p->giant_stride;
   int32_t n = 0;
-  if (sd.R > 0 && (e = launch_walk(L, st, &n)) != cudaSuccess) return e;
-  if ((e = launch_row_scan(sd.R, w, st)) != cudaSuccess) return e;
+  if (sd.R > 0) PLAN_TRY(launch_walk(L, st, &n));
+  PLAN_TRY(launch_row_scan(sd.R, w, st));
   if (p->pairs > 0) {
-    if ((e = launch_gather(0, sd.R, w, p->out_i, p->out_j, p->out_w, L.a.unweighted, st)) !=
-        cudaSuccess)
-      return e;
-    if ((e = launch_localize(p->out_i, p->out_j, p->pairs, p->row_base, p->count, w.row_ptr,
-                             p->offsets, st)) != cudaSuccess)
-      return e;
+    PLAN_TRY(launch_gather(0, sd.R, w, p->out_i, p->out_j, p->out_w, L.a.unweighted,
+                           p->pairs, st));
+    PLAN_TRY(launch_localize(p->out_i, p->out_j, p->pairs, p->row_base, p->count, w.row_ptr,
+                             p->offsets, st));
   } else {
-    if ((e = cudaMemsetAsync(p->offsets, 0, sizeof(long long) * (p->count + 1), st)) !=
-        cudaSuccess)
-      return e;
+    PLAN_TRY(cudaMemsetAsync(p->offsets, 0, sizeof(long long) * (p->count + 1), st));
   }
   if (launches) *launches = 1 + 2 + 1 + 4 + 1 + n + 3 + 2;
   return cudaSuccess;
 }
+#undef PLAN_TRY
 
 }  // namespace
 }  // namespace slg
@@ -1159,6 +1212,8 @@ const char *slg_strerror(int status) {
 
 int slg_abi_version(void) { return SLG_ABI_VERSION; }
 
+int slg_last_error_where(void) { return t_err_where; }
+
 }  // extern "C"
 
 extern "C" int slg_plan_create(const slg_hypergraph *hs, const int32_t *s, int32_t count,
@@ -1271,11 +1326,27 @@ extern "C" int slg_plan_create(const slg_hypergraph *hs, const int32_t *s, int32
       cudaError_t e = enqueue_plan(p.get(), b, st, nullptr);
       cudaEventRecord(t1, st);
       if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+      Meta *mh = nullptr;
+      if (e == cudaSuccess) e = thread_meta(&mh);
+      if (e == cudaSuccess) e = cudaMemcpy(mh, w.meta, sizeof(Meta), cudaMemcpyDeviceToHost);
       if (e != cudaSuccess) {
         cudaEventDestroy(t0);
         cudaEventDestroy(t1);
         cudaGetLastError();
         return status_of(e);
+      }
+      // every candidate must reproduce the counted pairs exactly
+      if (mh->err || mh->stage_overflow || (int64_t)mh->pairs != pairs) {
+        if (debug_on())
+          std::fprintf(stderr,
+                       "slg: plan candidate %d/%d/%d: err %d at %d, staging overflow %llu, "
+                       "pairs %llu, counted %lld\n",
+                       b.warp, b.ctas, b.ctal, mh->err, mh->err_where, mh->stage_overflow,
+                       mh->pairs, (long long)pairs);
+        t_err_where = mh->err ? mh->err_where : kWhereStage;
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+        return mh->err ? mh->err : SLG_ERR_INVALID;
       }
       float t = 0.f;
       cudaEventElapsedTime(&t, t0, t1);

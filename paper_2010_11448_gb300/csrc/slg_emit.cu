@@ -83,7 +83,8 @@ __global__ __launch_bounds__(kNT) void k_gather(int32_t row_begin, int32_t rows,
                                                 int32_t *__restrict__ out_i,
                                                 int32_t *__restrict__ out_j,
                                                 int32_t *__restrict__ out_w, int unweighted,
-                                                const Meta *meta) {
+                                                long long stage_cap, long long out_cap,
+                                                Meta *meta) {
   if (meta->err) return;
   __shared__ long long s_ptr[kGatherRows + 1];
   __shared__ long long s_sp[kGatherRows];
@@ -101,6 +102,10 @@ __global__ __launch_bounds__(kNT) void k_gather(int32_t row_begin, int32_t rows,
       else hi = mid;
     }
     const long long src = s_sp[lo] + (p - s_ptr[lo]);
+    if (s_sp[lo] < 0 || src >= stage_cap || p >= out_cap) {  // more pairs than counted
+      raise_error(meta, SLG_ERR_INVALID, kWhereStage);
+      continue;
+    }
     out_i[p] = row_begin + r0 + lo;
     out_j[p] = stage_j[src];
     if (!unweighted) out_w[p] = stage_w[src];
@@ -119,11 +124,12 @@ cudaError_t launch_row_scan(int32_t rows, const Work &w, cudaStream_t st) {
 }
 
 cudaError_t launch_gather(int32_t row_begin, int32_t rows, const Work &w, int32_t *out_i,
-                          int32_t *out_j, int32_t *out_w, int unweighted, cudaStream_t st) {
+                          int32_t *out_j, int32_t *out_w, int unweighted, long long out_cap,
+                          cudaStream_t st) {
   if (rows <= 0) return cudaSuccess;
   const int grid = (rows + kGatherRows - 1) / kGatherRows;
   k_gather<<<grid, kNT, 0, st>>>(row_begin, rows, w.row_ptr, w.stage_pos, w.stage_j, w.stage_w,
-                                 out_i, out_j, out_w, unweighted, w.meta);
+                                 out_i, out_j, out_w, unweighted, w.stage_cap, out_cap, w.meta);
   return cudaGetLastError();
 }
 

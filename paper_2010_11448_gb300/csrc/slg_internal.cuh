@@ -53,7 +53,7 @@ struct Meta {
 // Where a device-side check fired (for error reports).
 enum Where : int32_t {
   kWhereNone = 0, kWhereRowOffsets = 1, kWhereRowIds = 2, kWhereColOffsets = 3,
-  kWhereColIds = 4, kWhereMismatch = 5, kWhereHash = 6, kWhereGiant = 7,
+  kWhereColIds = 4, kWhereMismatch = 5, kWhereHash = 6, kWhereGiant = 7, kWhereStage = 8,
 };
 
 __device__ __forceinline__ void raise_error(Meta *meta, int32_t status, int32_t where) {
@@ -343,8 +343,10 @@ constexpr int32_t kGiantMaxR = 1 << 24;
 cudaError_t launch_walk(const WalkLaunch &L, cudaStream_t st, int32_t *launches,
                         cudaEvent_t *ev = nullptr);
 cudaError_t launch_row_scan(int32_t rows, const Work &w, cudaStream_t st);
+// out_cap: entries of the output arrays (a row beyond them raises an error).
 cudaError_t launch_gather(int32_t row_begin, int32_t rows, const Work &w, int32_t *out_i,
-                          int32_t *out_j, int32_t *out_w, int unweighted, cudaStream_t st);
+                          int32_t *out_j, int32_t *out_w, int unweighted, long long out_cap,
+                          cudaStream_t st);
 
 // Batched form (slg_plan.cu): union of many hypergraphs.
 struct BatchGraph {            // one member, device pointers

@@ -628,6 +628,10 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
     if (a.mode == kDirect) base = a.row_ptr[e - a.row_begin];
     int32_t out = 0;  // pairs of the row so far
     for (int32_t F0 = f_lo; F0 < R; F0 += chunk_w) {
+      // An empty bucket is skipped without a barrier, so threads may still
+      // be reading the previous super-chunk's sub[] / bstart[] here: every
+      // thread must be done with them before they are rewritten.
+      __syncthreads();
       const long long c0 = clock64();
       const int32_t F1 = (R - F0 > chunk_w) ? F0 + chunk_w : R;
       const int32_t nsb = ((F1 - F0 - 1) >> shift) + 1;

@@ -26,7 +26,8 @@ import time
 
 import numpy as np
 
-from . import DeviceHypergraph, alloc_outputs, build, count, filter_pairs, last_stats, wedges
+from . import (DeviceHypergraph, SlgError, alloc_outputs, build, count, filter_pairs,
+               last_stats, wedges)
 
 
 class Query:
@@ -163,20 +164,32 @@ class Server:
             try:
                 g = self.graphs[q.gid]
                 key = (q.gid, q.s, q.dual)
-                with self.cv:
-                    base = self._cached_for(q)
-                with torch.cuda.stream(st):
-                    if base is not None:
-                        i, j, w = filter_pairs(*base[1], q.s, stream=st)
-                        q.reused = True
-                    else:
-                        n = self.pair_cache.get(key)
-                        if n is None:
-                            n = count(g, q.s, q.dual, stream=st)
-                            self.pair_cache[key] = n
-                        out = alloc_outputs(n, False, g.e_off.device)
-                        i, j, w = build(g, q.s, dual=q.dual, out=out, stream=st)
-                    st.synchronize()
+                for attempt in (0, 1):
+                    with self.cv:
+                        base = self._cached_for(q)
+                    try:
+                        with torch.cuda.stream(st):
+                            if base is not None:
+                                i, j, w = filter_pairs(*base[1], q.s, stream=st)
+                                q.reused = True
+                            else:
+                                n = self.pair_cache.get(key)
+                                if n is None:
+                                    n = count(g, q.s, q.dual, stream=st)
+                                    self.pair_cache[key] = n
+                                out = alloc_outputs(n, False, g.e_off.device)
+                                i, j, w = build(g, q.s, dual=q.dual, out=out, stream=st)
+                            st.synchronize()
+                        break
+                    except (SlgError, torch.cuda.OutOfMemoryError) as exc:
+                        # out of device memory: give the kept lists back, retry once
+                        if attempt or getattr(exc, "status", 3) != 3 or not self.reuse:
+                            raise
+                        base = out = None
+                        with self.cv:
+                            self.cached.clear()
+                            self.cache_used = 0
+                        torch.cuda.empty_cache()
                 if self.reuse and base is None:
                     self._keep_list(q, (i, j, w))
                 q.pairs = int(i.shape[0])

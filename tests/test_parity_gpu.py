@@ -254,3 +254,23 @@ def test_chung_lu_1m_sampled_rows(chung_lu_1m, dual, s):
     sizes = torch.from_numpy(sizes_np.astype(np.int32)).to(i.device)
     assert bool(torch.all(sizes[i.long()] >= s)) and bool(torch.all(sizes[j.long()] >= s))
     assert slg.last_stats()["wedges"] == oracle.wedges(m, n, off, idx, s)
+
+
+def test_ids_beyond_one_super_chunk():
+    # the dual of 1500 large hyperedges over 5M vertices: rows are vertices,
+    # far-end ids span up to 5M, beyond the 4M ids one super-chunk of the
+    # giant bin covers, so giant rows cross several super-chunks
+    h = hg.uniform(1500, 5_000_000, 500, 6000, seed=9)
+    dh = slg.to_device(h)
+    m, n, off, idx = oracle.side(h, True)
+    deg = np.diff(off)
+    top = np.argsort(-deg, kind="stable")[:3000]
+    rows = np.unique(np.concatenate([top, np.arange(0, m, 97)])).astype(np.int32)
+    for s in (2, 3):
+        got = gpu_lg(dh, s, dual=True)
+        st = slg.last_stats()
+        assert st["rows_bin"][3] > 0  # giant rows present
+        sel = got[np.isin(got[:, 0], rows)]
+        want = oracle.canonical(*oracle.line_graph(m, n, off, idx, s, rows=rows, threads=16))
+        assert np.array_equal(sel, want), s
+        assert got.shape[0] == slg.count(dh, s, dual=True)
