@@ -66,3 +66,27 @@ def test_unweighted_batch_pairs():
         want = oracle.canonical(*oracle.line_graph_of(g, s))
         got = np.stack([i.cpu().numpy(), j.cpu().numpy()], 1) if i.shape[0] else np.zeros((0, 2))
         assert np.array_equal(got, want[:, :2])
+
+
+def test_union_beyond_one_super_chunk():
+    # two members with giant rows first, then a filler of 4.2M small rows:
+    # the union has more than 4M rows, so the early rows' id span covers
+    # several super-chunks of the giant bin while all their far ends lie in
+    # the first one (the later super-chunks are empty for them)
+    gs = [hg.chung_lu(20_000, 40_000, seed=61, size_cap=4000),
+          hg.lognormal_web(20_000, 40_000, seed=62, cap=2000, core_edges=256,
+                           core_vertices=512, core_density=0.3),
+          hg.uniform(4_200_000, 600_000, 1, 3, seed=3)]
+    ss = [2, 3, 2]
+    dhs = [slg.to_device(h) for h in gs]
+    plan = slg.Plan(dhs, ss)
+    for _ in range(3):
+        plan.execute()
+    res = plan.results()
+    for k in range(2):
+        want = oracle.canonical(*oracle.line_graph_of(gs[k], ss[k], threads=16))
+        assert np.array_equal(as_np(res[k]), want), k
+        st = slg.build(dhs[k], ss[k])
+        assert np.array_equal(as_np(st), want), k
+    filler = slg.build(dhs[2], ss[2])
+    assert all(torch.equal(a, b) for a, b in zip(res[2], filler))
