@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--builds", default="all",
                     help="comma list of builds to run, e.g. 'H:8,H*:2' (profiling)")
     ap.add_argument("--mode", choices=["headline", "batch", "serve", "core", "sweep", "ablation",
-                                       "post"],
+                                       "post", "table"],
                     default="headline",
                     help="headline: the Chung-Lu build (default); batch: many hypergraphs "
                          "in one captured pipeline vs sequential builds; serve: Poisson "
@@ -755,6 +755,93 @@ def run_post(args):
     return 0
 
 
+def run_table(args):
+    """Per-config table: for the small config and the headline workload,
+    each side and threshold (s = 1 of the headline workload counted only):
+    sizes, W_s, pairs, ms of the binned build (and
+    of the plain kernel and the filtered SpGEMM at s = 2, 8 on the headline
+    workload), wedges/s, the walk's algorithmic GB/s, and a bit-exact check
+    against the oracle (all rows of the small config; every 97th row plus
+    the 64 largest of the headline workload)."""
+    import numpy as np
+    import hypergen
+    import oracle
+    torch, slg = _setup_gpu()
+    peak, _ = peaks()
+    out = {}
+
+    def timed(fn, reps=3):
+        if reps > 1:
+            fn()
+        best = None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            r = fn()
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t) * 1e3
+            best = ms if best is None or ms < best else best
+        return best, r
+
+    for cname, svals, extra_s in (("uniform_2k", (1, 2, 3), ()),
+                                  (WORKLOAD, (2, 4, 8, 16), (2, 8))):
+        h = hypergen.config(cname) if cname != WORKLOAD else make_workload(0, 1.0)
+        dh = slg.to_device(h)
+        for dual in (False, True):
+            if cname == WORKLOAD:  # L_1 is counted only (billions of pairs)
+                t0 = time.perf_counter()
+                P1 = slg.count(dh, 1, dual)
+                out[f"{cname} {'H*' if dual else 'H'} s=1"] = {
+                    "pairs": int(P1), "count_ms": (time.perf_counter() - t0) * 1e3}
+            m, n, off, idx = oracle.side(h, dual)
+            sizes = np.diff(off)
+            degs = np.bincount(idx, minlength=n)
+            for sv in svals:
+                P = slg.count(dh, sv, dual)
+                o = slg.alloc_outputs(P)
+                slg.set_profiling(True)
+                ms, res = timed(lambda: slg.build(dh, sv, dual=dual, out=o))
+                st = slg.last_stats()
+                slg.set_profiling(False)
+                W = st["wedges"]
+                walk_ms = sum(st["ms_walk"])
+                wbytes = sum(walk_bytes(st, b) for b in range(4))
+                if cname == "uniform_2k":
+                    rows = None
+                    sel = res
+                else:
+                    big = np.argsort(-sizes, kind="stable")[:64]
+                    rows = np.unique(np.concatenate([np.arange(0, m, 97), big])).astype(np.int32)
+                    keep = torch.isin(res[0], torch.from_numpy(rows).to(res[0].device))
+                    sel = tuple(x[keep] for x in res)
+                i, j, w = (x.cpu().numpy() for x in sel)
+                want = oracle.canonical(*oracle.line_graph(m, n, off, idx, sv, rows=rows,
+                                                           threads=os.cpu_count() or 1))
+                got = np.stack([i, j, w], 1).astype(np.int64)
+                row = {"nnz": int(h.nnz), "max_size": int(sizes.max()), "max_degree": int(degs.max()),
+                       "W_s": int(W), "pairs": int(P), "binned_ms": ms,
+                       "wedges_per_s": W / (ms / 1e3), "pairs_per_s": P / (ms / 1e3),
+                       "walk_GBps_algorithmic": wbytes / (walk_ms / 1e3) / 1e9 if walk_ms else None,
+                       "walk_frac_of_peak": (wbytes / (walk_ms / 1e3) / 1e9 / peak) if walk_ms else None,
+                       "bit_exact": bool(np.array_equal(got, want)),
+                       "checked_rows": "all" if rows is None else int(rows.size)}
+                if sv in extra_s:
+                    o2 = slg.alloc_outputs(P)
+                    for algo in ("plain", "spgemm"):
+                        ms_a, ra = timed(lambda: slg.build(dh, sv, dual=dual, algo=algo, out=o2),
+                                         reps=1)
+                        row[algo + "_ms"] = ms_a
+                        row[algo + "_same"] = all(torch.equal(a, b) for a, b in zip(ra, res))
+                        o2[0].fill_(-1)
+                    del o2
+                out[f"{cname} {'H*' if dual else 'H'} s={sv}"] = row
+                del o, res
+                torch.cuda.empty_cache()
+    print(json.dumps({"mode": "table", "metric": "per-config build table", "peak_GBps": peak,
+                      "rows": out}), flush=True)
+    return 0
+
+
 def main():
     global _ONLY
     args = parse()
@@ -777,6 +864,8 @@ def main():
         return run_ablation(args)
     if args.mode == "post":
         return run_post(args)
+    if args.mode == "table":
+        return run_table(args)
     return run_ours(args)
 
 
