@@ -169,6 +169,31 @@ def test_host_entry_point(medium):
     assert np.array_equal(np.stack([a for a in got], 1).astype(np.int64), want)
 
 
+def test_host_entry_point_pinned(medium):
+    # page-locked host buffers in and out, as the end-to-end benchmark uses
+    h, _ = medium
+    for dual, s in ((False, 2), (True, 3)):
+        want = want_lg(h, s, dual)
+        cap = want.shape[0] + 7
+        out = tuple(torch.full((cap,), -1, dtype=torch.int32).pin_memory() for _ in range(3))
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).pin_memory()
+
+        class HostH:
+            pass
+        hh = HostH()
+        hh.m, hh.n = h.m, h.n
+        hh.e_off, hh.e_idx, hh.v_off, hh.v_idx = (pin(h.e_off), pin(h.e_idx), pin(h.v_off),
+                                                  pin(h.v_idx))
+        got = slg.build_host(hh, s, dual=dual, out=out)
+        assert np.array_equal(np.stack([a.numpy() for a in got], 1).astype(np.int64), want)
+        assert int(out[0][want.shape[0]]) == -1  # nothing written past the pairs
+        # too small: the count comes back, nothing overruns
+        small = tuple(torch.zeros(3, dtype=torch.int32).pin_memory() for _ in range(3))
+        with pytest.raises(slg.SlgError) as ei:
+            slg.build_host(hh, s, dual=dual, out=small)
+        assert ei.value.status == 2 and ei.value.needed == want.shape[0]
+
+
 def test_on_side_stream(medium):
     h, dh = medium
     st = torch.cuda.Stream()
