@@ -757,7 +757,8 @@ def run_post(args):
 
 def run_table(args):
     """Per-config table: for the small config and the headline workload,
-    each side and threshold (s = 1 of the headline workload counted only):
+    each side and threshold (s = 1 of the headline workload streamed in row
+    ranges of at most 4e8 pairs, checked against the closed form):
     sizes, W_s, pairs, ms of the binned build (and
     of the plain kernel and the filtered SpGEMM at s = 2, 8 on the headline
     workload), wedges/s, the walk's algorithmic GB/s, and a bit-exact check
@@ -788,11 +789,26 @@ def run_table(args):
         h = hypergen.config(cname) if cname != WORKLOAD else make_workload(0, 1.0)
         dh = slg.to_device(h)
         for dual in (False, True):
-            if cname == WORKLOAD:  # L_1 is counted only (billions of pairs)
+            if cname == WORKLOAD:  # L_1: billions of pairs, built in row ranges
+                torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 P1 = slg.count(dh, 1, dual)
+                count_ms = (time.perf_counter() - t0) * 1e3
+                _, n1, _, idx1 = oracle.side(h, dual)
+                d = np.bincount(idx1, minlength=n1).astype(np.int64)
+                t0 = time.perf_counter()
+                tp, tw, chunks = 0, 0, 0
+                for _, _, i1, _, w1 in slg.build_stream(dh, 1, 400_000_000, dual=dual):
+                    tp += int(i1.shape[0])
+                    tw += int(w1.sum(dtype=torch.int64))
+                    chunks += 1
+                torch.cuda.synchronize()
+                st_ms = (time.perf_counter() - t0) * 1e3
                 out[f"{cname} {'H*' if dual else 'H'} s=1"] = {
-                    "pairs": int(P1), "count_ms": (time.perf_counter() - t0) * 1e3}
+                    "pairs": int(P1), "count_ms": count_ms, "streamed_ms": st_ms,
+                    "chunks": chunks, "streamed_pairs_per_s": tp / (st_ms / 1e3),
+                    "weights_equal_closed_form": tw == int((d * (d - 1) // 2).sum()),
+                    "pairs_equal_count": tp == P1}
             m, n, off, idx = oracle.side(h, dual)
             sizes = np.diff(off)
             degs = np.bincount(idx, minlength=n)

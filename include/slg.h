@@ -155,6 +155,19 @@ int slg_build_rows(const slg_hypergraph *h, int32_t s, uint32_t flags,
                    int64_t *n_pairs, void *stream);
 
 /*
+ * slg_row_offsets -- where every row's pairs start in the canonical edge
+ * list: row_ptr[r] = number of pairs (i, j) with i < r, row_ptr[R] = |L_s|
+ * (one counting walk).  With it, an edge list too large for memory is
+ * built in row ranges of bounded size with slg_build_rows.
+ *   row_ptr  DEVICE int64 array of R + 1 entries (R = rows of the side)
+ *   flags    SLG_DUAL, SLG_UNWEIGHTED, SLG_TENSOR_CORE, SLG_NO_PRUNE; binned
+ *            algorithm only, no relabelling (SLG_ERR_UNSUPPORTED)
+ * Synchronises `stream`.  Errors as for slg_count.
+ */
+int slg_row_offsets(const slg_hypergraph *h, int32_t s, uint32_t flags,
+                    int64_t *row_ptr, void *stream);
+
+/*
  * slg_build_host -- slg_build with every array in HOST memory: the call
  * copies the incidence to the device, builds L_s there and copies the
  * triples back (end-to-end use from host data).  `h` holds host pointers.

@@ -21,7 +21,8 @@ import numpy as np
 __all__ = [
     "DeviceHypergraph", "to_device", "count", "build", "build_rows",
     "build_host", "wedges", "last_stats", "set_profiling", "tile_overlap",
-    "filter_pairs", "build_sweep", "squeeze", "adjacency", "components",
+    "filter_pairs", "build_sweep", "squeeze", "adjacency", "components", "row_offsets",
+    "build_stream",
     "set_core_params", "SLG_TENSOR_CORE", "SLG_RELABEL_ASC", "SLG_RELABEL_DESC",
     "SLG_NO_PRUNE",
     "Plan", "alloc_outputs",
@@ -105,6 +106,7 @@ ABI_FUNCTIONS = {
     "slg_build_host": (ctypes.c_int, [_HP, ctypes.c_int32, ctypes.c_uint32, _VP, _VP,
                                       _VP, ctypes.c_int64, _I64P, _VP]),
     "slg_wedges": (ctypes.c_int, [_HP, ctypes.c_int32, ctypes.c_uint32, _I64P, _VP]),
+    "slg_row_offsets": (ctypes.c_int, [_HP, ctypes.c_int32, ctypes.c_uint32, _VP, _VP]),
     "slg_last_stats": (ctypes.c_int, [ctypes.POINTER(_Stats)]),
     "slg_set_profiling": (ctypes.c_int, [ctypes.c_int]),
     "slg_set_core_params": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_float]),
@@ -326,6 +328,49 @@ def build_host(h, s: int, dual=False, unweighted=False, algo="binned",
         raise err
     p = int(n.value)
     return oi[:p], oj[:p], (ow[:p] if ow is not None else None)
+
+
+def row_offsets(h: DeviceHypergraph, s: int, dual=False, unweighted=False, stream=None,
+                tensor=False, prune=True):
+    """int64 CUDA tensor [R + 1]: where each row's pairs start in the
+    canonical edge list (slg_row_offsets)."""
+    import torch
+    R = h.rows(dual)
+    ptr = torch.empty(R + 1, dtype=torch.int64, device=h.e_off.device)
+    rc = load().slg_row_offsets(ctypes.byref(h.struct), int(s),
+                                _flags(dual, unweighted, "binned", tensor, None, prune),
+                                ptr.data_ptr(), _stream(stream))
+    if rc != 0:
+        raise SlgError(rc, "slg_row_offsets")
+    return ptr
+
+
+def build_stream(h: DeviceHypergraph, s: int, max_pairs: int, dual=False, unweighted=False,
+                 stream=None, tensor=False):
+    """The canonical edge list in consecutive row ranges of at most
+    ``max_pairs`` pairs each (a single larger row forms its own range).
+    Yields (row_begin, row_end, i, j, w); the tensors are views of one
+    output buffer that the next chunk overwrites."""
+    import numpy as np
+    ptr = row_offsets(h, s, dual, unweighted, stream, tensor).cpu().numpy()
+    R = len(ptr) - 1
+    biggest = int(np.diff(ptr).max()) if R else 0
+    out = _outputs(max(int(max_pairs), biggest), unweighted, h.e_off.device)
+    flags = _flags(dual, unweighted, "binned", tensor)
+    a = 0
+    while a < R:
+        b = int(np.searchsorted(ptr, ptr[a] + max_pairs, side="right")) - 1
+        b = min(max(b, a + 1), R)
+        n = ctypes.c_int64(0)
+        rc = load().slg_build_rows(ctypes.byref(h.struct), int(s), flags, a, b,
+                                   out[0].data_ptr(), out[1].data_ptr(),
+                                   out[2].data_ptr() if out[2] is not None else None,
+                                   int(out[0].shape[0]), ctypes.byref(n), _stream(stream))
+        if rc != 0:
+            raise SlgError(rc, "slg_build_rows")
+        p = int(n.value)
+        yield a, b, out[0][:p], out[1][:p], (out[2][:p] if out[2] is not None else None)
+        a = b
 
 
 def wedges(h: DeviceHypergraph, s: int, dual=False, stream=None) -> int:

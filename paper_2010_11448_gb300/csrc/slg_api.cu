@@ -631,7 +631,7 @@ int run_spgemm(Call &c, int64_t *result) {
 int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin,
         int32_t row_end, Op op, int32_t *out_i, int32_t *out_j, int32_t *out_w,
         int64_t capacity, int64_t *result, cudaStream_t st, const int32_t *row_s = nullptr,
-        int32_t *max_row_work = nullptr) {
+        int32_t *max_row_work = nullptr, long long *row_ptr_out = nullptr) {
   int rc = check_args(h, smin, flags);
   if (rc != SLG_OK) return rc;
   if (!result) return SLG_ERR_INVALID;
@@ -730,6 +730,11 @@ int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin
   else rc = run_binned(c, &value);
   if (rc == SLG_OK || rc == SLG_ERR_CAPACITY) *result = value;
   if (rc != SLG_OK) return rc;
+  if (row_ptr_out) {
+    SLG_TRY(cudaMemcpyAsync(row_ptr_out, w.row_ptr, sizeof(long long) * ((size_t)c.rows + 1),
+                            cudaMemcpyDeviceToDevice, st));
+    SLG_TRY(cudaStreamSynchronize(st));
+  }
 
   // Relabelled pairs -> caller ids in canonical (i, j) order.
   if (perm && op == kOpBuild && value > 0) {
@@ -922,6 +927,18 @@ int slg_build_rows(const slg_hypergraph *h, int32_t s, uint32_t flags, int32_t r
                    int64_t capacity, int64_t *n_pairs, void *stream) {
   return run(h, s, flags, row_begin, row_end, kOpBuild, out_i, out_j, out_w, capacity, n_pairs,
              (cudaStream_t)stream);
+}
+
+int slg_row_offsets(const slg_hypergraph *h, int32_t s, uint32_t flags, int64_t *row_ptr,
+                    void *stream) {
+  if (!h || !row_ptr) return SLG_ERR_INVALID;
+  if ((flags & SLG_ALGO_MASK) != SLG_ALGO_BINNED ||
+      (flags & (SLG_RELABEL_ASC | SLG_RELABEL_DESC)))
+    return SLG_ERR_UNSUPPORTED;
+  const int32_t R = (flags & SLG_DUAL) ? h->n_vertices : h->n_edges;
+  int64_t pairs = 0;
+  return run(h, s, flags, 0, R, kOpCount, nullptr, nullptr, nullptr, 0, &pairs,
+             (cudaStream_t)stream, nullptr, nullptr, reinterpret_cast<long long *>(row_ptr));
 }
 
 int slg_wedges(const slg_hypergraph *h, int32_t s, uint32_t flags, int64_t *wedges,
