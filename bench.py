@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--builds", default="all",
                     help="comma list of builds to run, e.g. 'H:8,H*:2' (profiling)")
     ap.add_argument("--mode", choices=["headline", "batch", "serve", "core", "sweep", "ablation",
-                                       "post", "table"],
+                                       "post", "table", "atomics"],
                     default="headline",
                     help="headline: the Chung-Lu build (default); batch: many hypergraphs "
                          "in one captured pipeline vs sequential builds; serve: Poisson "
@@ -858,6 +858,26 @@ def run_table(args):
     return 0
 
 
+def run_atomics(args):
+    """Shared-memory atomic throughput on random slots (the ceiling of the
+    per-row hash tables): compiles csrc/micro/shared_atomics.cu with nvcc
+    for sm_103a and runs it."""
+    import tempfile
+    from paper_2010_11448_gb300 import build_lib
+    src = os.path.join(ROOT, "paper_2010_11448_gb300", "csrc", "micro", "shared_atomics.cu")
+    with tempfile.TemporaryDirectory() as d:
+        exe = os.path.join(d, "shared_atomics")
+        subprocess.run([build_lib.nvcc(), *build_lib.ARCH, "-O3", "-o", exe, src], check=True)
+        r = subprocess.run([exe], check=True, capture_output=True, text=True)
+    rows = [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
+    clock_ghz, sms = 2.07, 152
+    for x in rows:
+        x["ops_per_s"] = x["ops_per_cycle_per_sm"] * sms * clock_ghz * 1e9
+    print(json.dumps({"mode": "atomics", "metric": "shared-memory ops per SM cycle, random "
+                      "slots of a 64 KB table", "rows": rows}), flush=True)
+    return 0
+
+
 def main():
     global _ONLY
     args = parse()
@@ -882,6 +902,8 @@ def main():
         return run_post(args)
     if args.mode == "table":
         return run_table(args)
+    if args.mode == "atomics":
+        return run_atomics(args)
     return run_ours(args)
 
 

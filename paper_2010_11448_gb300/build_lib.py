@@ -38,7 +38,7 @@ def _sources():
 
 def _stamp(extra_flags) -> str:
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(CSRC, "*")) +
+    for f in sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
                     glob.glob(os.path.join(INCLUDE, "*.h"))):
         h.update(f.encode())
         with open(f, "rb") as fh:
