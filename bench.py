@@ -237,6 +237,29 @@ def cpu_oracle_rate(h, stride: int):
     return total_w / total_t, total_t / stride, cores, sample
 
 
+def gpu_local_cpus(dev):
+    """Host CPUs attached to the GPU's NUMA node (from sysfs), or None."""
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(dev)
+        bus = f"{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+        base = f"/sys/bus/pci/devices/{bus}"
+        node = int(open(os.path.join(base, "numa_node")).read().strip())
+        path = (f"/sys/devices/system/node/node{node}/cpulist" if node >= 0
+                else os.path.join(base, "local_cpulist"))
+        cpus = set()
+        for part in open(path).read().strip().split(","):
+            if "-" in part:
+                a, b = part.split("-")
+                cpus.update(range(int(a), int(b) + 1))
+            elif part:
+                cpus.add(int(part))
+        cpus &= os.sched_getaffinity(0)
+        return cpus or None
+    except Exception:
+        return None
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -393,8 +416,13 @@ def run_ours(args):
         per[f"{'H*' if dual else 'H'} s={s}"] = (time.perf_counter() - t0) * 1e3
     result["build_ms"] = per
 
-    # end to end through the C ABI with host buffers (pinned)
+    # end to end through the C ABI with host buffers (pinned), allocated and
+    # driven from the host cores local to the GPU when the system says which
     if not args.no_e2e:
+        host_cpus = gpu_local_cpus(dev)
+        saved_affinity = os.sched_getaffinity(0) if host_cpus else None
+        if host_cpus:
+            os.sched_setaffinity(0, host_cpus)
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).pin_memory()
 
         class HostH:
@@ -421,7 +449,12 @@ def run_ours(args):
         in_bytes = 4 * (h.m + 1 + h.n + 1 + 2 * h.nnz)
         result["e2e"] = {"value": u2 / (dt_max / 1e3), "unit": UNIT,
                          "h2d_bytes_per_step": in_bytes * len(J),
-                         "d2h_bytes_per_step": 12 * P_step, "steps": k2}
+                         "d2h_bytes_per_step": 12 * P_step, "steps": k2,
+                         "host_cpus": (f"{min(host_cpus)}-{max(host_cpus)}" if host_cpus
+                                       else "any")}
+        if saved_affinity:
+            os.sched_setaffinity(0, saved_affinity)
+        del houts, hh
 
     if rank == 0 and not args.no_cpu:
         oracle.build()

@@ -461,7 +461,9 @@ __global__ __launch_bounds__(NT, MINB) void k_walk_cta(Walk w, const int32_t *__
 // SM.  The row's far ends f lie in [f_lo, R) (f_lo = e + 1 for the
 // upper-triangle walk, 0 for whole columns).
 //   1. one load-balanced walk copies the row's far ends, in flattened wedge
-//      order, to the CTA's global scratch `flat` (coalesced stores);
+//      order, to the CTA's global scratch `flat` (coalesced stores); a row
+//      whose ids fit one super-chunk also counts its sub-range histogram
+//      during this walk;
 //   2. the id range is cut into super-chunks of at most kNSB sub-ranges of
 //      2^shift ids each (2^shift <= kGiantTMax / 4).  Per super-chunk: a pass
 //      over `flat` counts its wedges per sub-range (shared histogram), an
@@ -613,9 +615,24 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
       break;
     }
     long long clk0 = clock64();
-    // 1. flattened far ends
-    cta_walk<kGiantNT, 4>(w, w.r_off[e], w.r_off[e + 1], s_beg, s_pref, ws,
-                          [&](int32_t f, int32_t i) { flat[i] = f; });
+    // 1. flattened far ends; a row within one super-chunk also counts its
+    // sub-range histogram here (saving one pass over the copy)
+    const bool single = R - f_lo <= chunk_w;
+    if (single) {
+      for (int i = threadIdx.x; i < kNSB; i += kGiantNT) {
+        sub[i] = 0;
+        subt[i] = 0;
+      }
+      __syncthreads();
+      cta_walk<kGiantNT, 4>(w, w.r_off[e], w.r_off[e + 1], s_beg, s_pref, ws,
+                            [&](int32_t f, int32_t i) {
+                              flat[i] = f;
+                              atomicAdd(sub + ((f - f_lo) >> shift), 1);
+                            });
+    } else {
+      cta_walk<kGiantNT, 4>(w, w.r_off[e], w.r_off[e + 1], s_beg, s_pref, ws,
+                            [&](int32_t f, int32_t i) { flat[i] = f; });
+    }
     long long clk_part = 0, clk_bucket = 0;
     if (threadIdx.x == 0) atomicAdd(&meta->giant_cycles[0], (unsigned long long)(clock64() - clk0));
     // Core rows also receive tile items (f, |e ∩ f ∩ C_c|) for every active
@@ -636,14 +653,16 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
       const int32_t F1 = (R - F0 > chunk_w) ? F0 + chunk_w : R;
       const int32_t nsb = ((F1 - F0 - 1) >> shift) + 1;
       // 2. histograms of sub-ranges (wedges; tile items), scans, scatter
-      for (int i = threadIdx.x; i < kNSB; i += kGiantNT) {
-        sub[i] = 0;
-        subt[i] = 0;
+      if (!single) {
+        for (int i = threadIdx.x; i < kNSB; i += kGiantNT) {
+          sub[i] = 0;
+          subt[i] = 0;
+        }
+        __syncthreads();
+        for_each_batched<kGiantNT, 8>(flat, 0, work, [&](int32_t f) {
+          if (f >= F0 && f < F1) atomicAdd(sub + ((f - F0) >> shift), 1);
+        });
       }
-      __syncthreads();
-      for_each_batched<kGiantNT, 8>(flat, 0, work, [&](int32_t f) {
-        if (f >= F0 && f < F1) atomicAdd(sub + ((f - F0) >> shift), 1);
-      });
       if (core_row)
         for (int32_t p = ri + 1 + (int32_t)threadIdx.x; p < ci.n_core; p += kGiantNT) {
           const int32_t f = ci.core_list[p];
