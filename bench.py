@@ -54,6 +54,8 @@ def parse():
                     help="degree-ordered relabelling of the rows before the walk")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the plain-kernel and SpGEMM comparison builds")
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (testing)")
     ap.add_argument("--builds", default="all",
                     help="comma list of builds to run, e.g. 'H:8,H*:2' (profiling)")
@@ -415,6 +417,27 @@ def run_ours(args):
         slg.build(dh, s, dual=dual, algo=algo, out=outs[(dual, s)], relabel=rl)
         per[f"{'H*' if dual else 'H'} s={s}"] = (time.perf_counter() - t0) * 1e3
     result["build_ms"] = per
+
+    # the same builds with the plain per-hyperedge kernel and the filtered
+    # SpGEMM (one run each, outside the timed region; outputs compared)
+    if algo == "binned" and not args.no_compare:
+        comp = {}
+        for other in ("plain", "spgemm"):
+            ms_o, same = {}, True
+            for dual, s in J:
+                o2 = slg._outputs(caps[(dual, s)], False, dev)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r2 = slg.build(dh, s, dual=dual, algo=other, out=o2)
+                torch.cuda.synchronize()
+                ms_o[f"{'H*' if dual else 'H'} s={s}"] = (time.perf_counter() - t0) * 1e3
+                r1 = slg.build(dh, s, dual=dual, out=outs[(dual, s)])
+                same = same and all(torch.equal(a, b) for a, b in zip(r1, r2))
+                del o2, r2
+            comp[other] = {"build_ms": ms_o, "identical": same,
+                           "step_ms": sum(ms_o.values()),
+                           "binned_speedup": sum(ms_o.values()) / sum(per.values())}
+        result["comparison"] = comp
 
     # end to end through the C ABI with host buffers (pinned), allocated and
     # driven from the host cores local to the GPU when the system says which
