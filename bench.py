@@ -457,22 +457,55 @@ def run_ours(args):
         houts = {k: tuple(torch.empty(caps[k], dtype=torch.int32).pin_memory()
                           for _ in range(3)) for k in J}
 
-        def e2e_step():
-            for dual, s in J:
-                slg.build_host(hh, s, dual=dual, algo=algo, out=houts[(dual, s)], relabel=rl)
-        e2e_step()
+        streams = [torch.cuda.Stream(device=dev) for _ in J]
+
+        def e2e_step(overlap=True):
+            # one stream per build; with overlap each call returns once its
+            # copies back are enqueued (SLG_ASYNC), so one build's copies to
+            # the host run during the next build's walk; the step ends when
+            # every stream is done
+            for (dual, s), st in zip(J, streams):
+                slg.build_host(hh, s, dual=dual, algo=algo, out=houts[(dual, s)], relabel=rl,
+                               stream=st, wait=not overlap)
+            for st in streams:
+                st.synchronize()
+
+        def e2e_rate(overlap):
+            e2e_step(overlap)
+            torch.cuda.synchronize()
+            k2 = max(1, min(args.steps, 3))
+            t0 = time.perf_counter()
+            for _ in range(k2):
+                e2e_step(overlap)
+            torch.cuda.synchronize()
+            dt = (time.perf_counter() - t0) * 1e3
+            u2, dt_max = aggregate(W_step * k2, dt, world, dev)
+            return u2 / (dt_max / 1e3), k2
+        v_ov, k2 = e2e_rate(True)
+        v_serial, _ = e2e_rate(False)
+        # context for the host leg: one build at a time, wall ms per call, and
+        # the plain device-to-host copy rate into the same page-locked arrays
+        ms_calls = {}
+        for dual, s in J:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            slg.build_host(hh, s, dual=dual, algo=algo, out=houts[(dual, s)], relabel=rl)
+            ms_calls[f"{'H*' if dual else 'H'} s={s}"] = (time.perf_counter() - t0) * 1e3
         torch.cuda.synchronize()
-        k2 = max(1, min(args.steps, 3))
         t0 = time.perf_counter()
-        for _ in range(k2):
-            e2e_step()
+        for k in J:
+            for a, b in zip(houts[k], outs[k]):
+                a.copy_(b, non_blocking=True)
         torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) * 1e3
-        u2, dt_max = aggregate(W_step * k2, dt, world, dev)
+        d2h_gbs = 12 * P_step / (time.perf_counter() - t0) / 1e9
         in_bytes = 4 * (h.m + 1 + h.n + 1 + 2 * h.nnz)
-        result["e2e"] = {"value": u2 / (dt_max / 1e3), "unit": UNIT,
+        result["e2e"] = {"value": v_ov, "unit": UNIT,
                          "h2d_bytes_per_step": in_bytes * len(J),
                          "d2h_bytes_per_step": 12 * P_step, "steps": k2,
+                         "overlap": "one stream per build, SLG_ASYNC: copies back overlap "
+                                    "the next build",
+                         "value_one_build_at_a_time": v_serial,
+                         "ms_per_call": ms_calls, "d2h_copy_gbs": d2h_gbs,
                          "host_cpus": (f"{min(host_cpus)}-{max(host_cpus)}" if host_cpus
                                        else "any")}
         if saved_affinity:

@@ -102,6 +102,9 @@ typedef enum slg_status {
                                 walk at both ends): same result, more work.
                                 For ablations (Section V); binned algorithm
                                 only */
+#define SLG_ASYNC 0x40u      /* slg_build_host only: return once the copies
+                                of the result to the host are enqueued on
+                                `stream` (see slg_build_host) */
 /* Algorithm selector (mutually exclusive values in bits 8..11). */
 #define SLG_ALGO_MASK 0xF00u
 #define SLG_ALGO_BINNED 0x000u /* default: degree-binned wedge walk */
@@ -172,6 +175,12 @@ int slg_row_offsets(const slg_hypergraph *h, int32_t s, uint32_t flags,
  * copies the incidence to the device, builds L_s there and copies the
  * triples back (end-to-end use from host data).  `h` holds host pointers.
  * Pinned host memory makes the copies faster; pageable memory also works.
+ * The input arrays may be reused when the call returns.  Without SLG_ASYNC
+ * the call returns with out_i/out_j/out_w filled; with SLG_ASYNC it returns
+ * (with *n_pairs set) once their device-to-host copies are enqueued on
+ * `stream`: they are filled when the stream's work completes, so that calls
+ * on different streams overlap one build's copies with the next one's walk.
+ * Copy errors then surface when the stream is synchronised.
  */
 int slg_build_host(const slg_hypergraph *h, int32_t s, uint32_t flags,
                    int32_t *out_i, int32_t *out_j, int32_t *out_w,

@@ -37,6 +37,7 @@ SLG_TENSOR_CORE = 0x4
 SLG_RELABEL_ASC = 0x8
 SLG_RELABEL_DESC = 0x10
 SLG_NO_PRUNE = 0x20
+SLG_ASYNC = 0x40
 SLG_ALGO_BINNED = 0x000
 SLG_ALGO_PLAIN = 0x100
 SLG_ALGO_SPGEMM = 0x200
@@ -302,10 +303,12 @@ def build_rows(h: DeviceHypergraph, s: int, row_begin: int, row_end: int,
 
 
 def build_host(h, s: int, dual=False, unweighted=False, algo="binned",
-               capacity: int = 0, out=None, stream=None, relabel=None):
+               capacity: int = 0, out=None, stream=None, relabel=None, wait=True):
     """End-to-end from host arrays: ``h`` holds numpy (ideally pinned torch
     CPU) int32 arrays; the library copies them in, builds, copies back.
-    ``out`` = three host int32 arrays of the same capacity."""
+    ``out`` = three host int32 arrays of the same capacity.  wait=False
+    (SLG_ASYNC) returns once the copies back are enqueued on ``stream``: the
+    arrays are filled when that stream's work completes."""
     def ptr(a):
         if hasattr(a, "data_ptr"):
             return a.data_ptr()
@@ -318,8 +321,8 @@ def build_host(h, s: int, dual=False, unweighted=False, algo="binned",
                None if unweighted else np.empty(cap, np.int32))
     oi, oj, ow = out
     n = ctypes.c_int64(0)
-    rc = load().slg_build_host(ctypes.byref(st), int(s),
-                               _flags(dual, unweighted, algo, relabel=relabel),
+    flags = _flags(dual, unweighted, algo, relabel=relabel) | (0 if wait else SLG_ASYNC)
+    rc = load().slg_build_host(ctypes.byref(st), int(s), flags,
                                ptr(oi), ptr(oj), ptr(ow) if ow is not None else None,
                                int(oi.shape[0]), ctypes.byref(n), _stream(stream))
     if rc != 0:

@@ -19,13 +19,51 @@ constexpr int kMaxDevices = 64;
 // Per-device state kept between calls: the plain kernel's dense counters
 // (all zero between calls; the kernel restores the zeros it disturbs).
 struct DeviceCtx {
-  std::mutex mu;               // one-time set-up; the plain kernel's scratch
+  std::mutex mu;               // the plain kernel's scratch
   int32_t *giant = nullptr;    // plain kernel: per-warp zeroed counters
   size_t giant_elems = 0;
-  bool pool_ready = false;
+  std::mutex mem_mu;           // creation of `mem`
+  cudaMemPool_t mem = nullptr;  // the library's stream-ordered memory pool
 };
 
 DeviceCtx g_ctx[kMaxDevices];
+
+DeviceCtx &ctx_for_current(int *dev_out) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  *dev_out = dev;
+  return g_ctx[dev % kMaxDevices];
+}
+
+// The library's own stream-ordered memory pool on the current device,
+// created on first use.  Freed memory stays in it for the next call (release
+// threshold unlimited), and memory freed on one stream is reused on another
+// only once the free has completed: the pool never makes a call wait for
+// another stream's work, so calls on different streams overlap (e.g. one
+// build's copies to the host with the next build's walk).  Null if the pool
+// cannot be created (the device's default pool is used then).
+cudaMemPool_t lib_pool() {
+  int dev = 0;
+  DeviceCtx &c = ctx_for_current(&dev);
+  std::lock_guard<std::mutex> lock(c.mem_mu);
+  if (!c.mem) {
+    cudaMemPoolProps p = {};
+    p.allocType = cudaMemAllocationTypePinned;
+    p.handleTypes = cudaMemHandleTypeNone;
+    p.location.type = cudaMemLocationTypeDevice;
+    p.location.id = dev;
+    if (cudaMemPoolCreate(&c.mem, &p) == cudaSuccess) {
+      uint64_t thr = ~0ull;
+      cudaMemPoolSetAttribute(c.mem, cudaMemPoolAttrReleaseThreshold, &thr);
+      int off = 0;
+      cudaMemPoolSetAttribute(c.mem, cudaMemPoolReuseAllowInternalDependencies, &off);
+    } else {
+      c.mem = nullptr;
+    }
+    cudaGetLastError();
+  }
+  return c.mem;
+}
 thread_local slg_stats t_stats;
 thread_local int t_profile = 0;
 thread_local int32_t t_tau_c = 64, t_tau_r = 32;
@@ -67,35 +105,35 @@ int status_of(cudaError_t e) {
   return SLG_ERR_CUDA;
 }
 
-// The library's freed stream-ordered memory stays in the device's pool for
-// the next call (release threshold: unlimited).  When an allocation fails,
-// the pool's unused memory goes back to the driver and the allocation is
-// tried once more, so that memory the pool keeps never starves an
-// allocation (the pool's own, or a plain cudaMalloc).
+// When an allocation fails, the pool's unused memory goes back to the
+// driver and the allocation is tried once more, so that memory the pool
+// keeps never starves an allocation (the pool's own, or a plain cudaMalloc).
 void trim_pool() {
-  int dev = 0;
-  cudaMemPool_t pool;
-  if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess)
-    cudaMemPoolTrimTo(pool, 0);
+  cudaMemPool_t m = lib_pool();
+  if (m) cudaMemPoolTrimTo(m, 0);
   cudaGetLastError();
 }
 
 // Stream-ordered allocations released (stream-ordered) when the call ends.
 struct Pool {
   cudaStream_t st;
+  cudaMemPool_t mem;
   std::vector<void *> ptrs;
-  explicit Pool(cudaStream_t s) : st(s) {}
+  explicit Pool(cudaStream_t s) : st(s), mem(lib_pool()) {}
+  cudaError_t alloc(void **q, size_t bytes) {
+    return mem ? cudaMallocFromPoolAsync(q, bytes, mem, st) : cudaMallocAsync(q, bytes, st);
+  }
   template <class T>
   cudaError_t get(T **p, size_t count) {
     size_t bytes = count * sizeof(T);
     if (bytes < 16) bytes = 16;
     void *q = nullptr;
-    cudaError_t e = cudaMallocAsync(&q, bytes, st);
+    cudaError_t e = alloc(&q, bytes);
     if (e == cudaErrorMemoryAllocation) {
       cudaGetLastError();
       cudaStreamSynchronize(st);  // frees queued on the stream complete first
       trim_pool();
-      e = cudaMallocAsync(&q, bytes, st);
+      e = alloc(&q, bytes);
     }
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -172,25 +210,6 @@ Side side_of(const slg_hypergraph *h, uint32_t flags) {
   return s;
 }
 
-DeviceCtx &ctx_for_current(int *dev_out) {
-  int dev = 0;
-  cudaGetDevice(&dev);
-  *dev_out = dev;
-  return g_ctx[dev % kMaxDevices];
-}
-
-// Freed pool memory stays with the process instead of going back to the
-// driver after every call.
-void ensure_pool(DeviceCtx &c, int dev) {
-  if (c.pool_ready) return;
-  cudaMemPool_t pool;
-  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-    uint64_t thr = ~0ull;
-    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-  }
-  cudaGetLastError();
-  c.pool_ready = true;
-}
 
 cudaError_t ensure_giant(DeviceCtx &c, size_t elems, cudaStream_t st) {
   if (c.giant_elems >= elems) return cudaSuccess;
@@ -664,10 +683,6 @@ int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin
 
   int dev = 0;
   DeviceCtx &ctx = ctx_for_current(&dev);
-  {
-    std::lock_guard<std::mutex> lock(ctx.mu);
-    ensure_pool(ctx, dev);
-  }
   SLG_TRY(thread_meta(&c.meta_host));
   c.ctx = &ctx;
 
@@ -952,6 +967,8 @@ int slg_wedges(const slg_hypergraph *h, int32_t s, uint32_t flags, int64_t *wedg
 int slg_build_host(const slg_hypergraph *hh, int32_t s, uint32_t flags, int32_t *out_i,
                    int32_t *out_j, int32_t *out_w, int64_t capacity, int64_t *n_pairs,
                    void *stream) {
+  const bool async = (flags & SLG_ASYNC) != 0;
+  flags &= ~(uint32_t)SLG_ASYNC;
   int rc = check_args(hh, s, flags);
   if (rc != SLG_OK) return rc;
   if (!n_pairs || capacity < 0) return SLG_ERR_INVALID;
@@ -991,7 +1008,8 @@ int slg_build_host(const slg_hypergraph *hh, int32_t s, uint32_t flags, int32_t 
     if (!unweighted)
       SLG_TRY(cudaMemcpyAsync(out_w, ow, (size_t)pairs * 4, cudaMemcpyDeviceToHost, st));
   }
-  SLG_TRY(cudaStreamSynchronize(st));
+  // the device buffers are released after the copies, in stream order
+  if (!async) SLG_TRY(cudaStreamSynchronize(st));
   return SLG_OK;
 }
 

@@ -257,18 +257,47 @@ __device__ __forceinline__ int table_lg(int32_t distinct, int lg_max) {
   return lg < lg_max ? lg : lg_max;
 }
 
-#ifndef SLG_RANK_SORT_MAX
-#define SLG_RANK_SORT_MAX 512
-#endif
-constexpr int32_t kRankSortMax = SLG_RANK_SORT_MAX;
+// Ascending order of one key per lane across a warp: a bitonic network on
+// shuffles (for k = 32 every lane is in an ascending half).
+__device__ __forceinline__ unsigned long long warp_sort32(unsigned long long x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, j);
+      const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+      x = keep_min ? (x < y ? x : y) : (x < y ? y : x);
+    }
+  return x;
+}
 
-// Sorts keys[0, n) of the table region by f: by rank into [n, 2 n) when n
-// is small, else bitonic in place over [0, n2); returns where they are.
-// `*used` receives the end of the region touched.
+// Number of keys below x in a sorted run a[0, 32): branch-free binary search.
+__device__ __forceinline__ int32_t run_below(const unsigned long long *a, unsigned long long x) {
+  int32_t c = 0;
+#pragma unroll
+  for (int st = 16; st > 0; st >>= 1)
+    if (a[c + st - 1] < x) c += st;
+  return c + (a[c] < x);  // adds one only when c = 31 and all 32 are below
+}
+
+// Sorts the distinct keys tab[0, n) by f and returns where they are.
+//  - small n (<= 64 with 512 threads, <= 512 with fewer): each key's rank is
+//    the number of keys below it (one broadcast pass), written to [n, 2 n);
+//  - 512 threads, n <= 1024: each warp sorts runs of 32 keys in registers
+//    (padding ~0, above every key) and stores them back; a key's place is
+//    then the sum over all runs of the keys below it (its own run contributes
+//    its index), written to [32 nr, 32 nr + n) for nr = ceil(n / 32) runs.
+//    (Smaller blocks keep the rank pass: the run code's registers would cost
+//    them a resident block per SM.)
+//  - larger n: a bitonic sort in place over [0, n2), n2 = 2^ceil(log2 n).
+// `*used` receives the end of the region touched; it stays within
+// max(T, 2 n + 32) <= the table's capacity for T >= 2 n.
 template <int NT>
 __device__ __forceinline__ int32_t sort_survivors(unsigned long long *tab, int32_t n,
                                                   int32_t *used) {
-  if (n <= kRankSortMax) {
+  constexpr bool kRuns = NT >= 512;
+  if (n <= (kRuns ? 64 : 512)) {
     for (int32_t i = threadIdx.x; i < n; i += NT) {
       const unsigned long long x = tab[i];
       int32_t r = 0;
@@ -278,6 +307,35 @@ __device__ __forceinline__ int32_t sort_survivors(unsigned long long *tab, int32
     __syncthreads();
     *used = 2 * n;
     return n;
+  }
+  if constexpr (kRuns) {
+    if (n <= 2 * NT) {
+      const int32_t nr = (n + 31) >> 5;
+      for (int32_t r = (int32_t)threadIdx.x >> 5; r < nr; r += NT / 32) {
+        const int32_t i = (r << 5) + (int32_t)(threadIdx.x & 31);
+        const unsigned long long x = warp_sort32(i < n ? tab[i] : ~0ull);
+        tab[i] = x;  // the run's loads precede the shuffles
+      }
+      __syncthreads();
+      const int32_t out = nr << 5;
+      for (int32_t i = threadIdx.x; i < n; i += NT) {
+        const unsigned long long x = tab[i];
+        int32_t r = 0;
+        int32_t q = 0;
+        for (; q + 4 <= nr; q += 4) {
+          const int32_t c0 = run_below(tab + (q << 5), x);
+          const int32_t c1 = run_below(tab + ((q + 1) << 5), x);
+          const int32_t c2 = run_below(tab + ((q + 2) << 5), x);
+          const int32_t c3 = run_below(tab + ((q + 3) << 5), x);
+          r += c0 + c1 + c2 + c3;
+        }
+        for (; q < nr; ++q) r += run_below(tab + (q << 5), x);
+        tab[out + r] = x;
+      }
+      __syncthreads();
+      *used = out + n;
+      return out;
+    }
   }
   int32_t n2 = 1;
   while (n2 < n) n2 <<= 1;
@@ -310,10 +368,12 @@ __device__ __forceinline__ int32_t sort_survivors(unsigned long long *tab, int32
 // r lands below the number of qualifying slots seen so far, hence on a slot
 // of round r or earlier, all of which were read before the round's scan.
 // Returns the number of survivors; with `sort` they are in ascending f at
-// tab[*sorted_at, *sorted_at + count).
+// tab[*sorted_at, *sorted_at + count), and tab[0, *used) must be cleared
+// after use (table_reset_front).
 template <int NT, int SPT>
 __device__ __forceinline__ int32_t table_collect(unsigned long long *tab, int32_t T, int32_t smin,
-                                                 bool sort, int32_t *ws, int32_t *sorted_at) {
+                                                 bool sort, int32_t *ws, int32_t *sorted_at,
+                                                 int32_t *used) {
   constexpr int RND = SPT < 8 ? SPT : 8;
   int32_t run = 0;
   for (int32_t r0 = 0; r0 * NT < T; r0 += RND) {
@@ -335,12 +395,23 @@ __device__ __forceinline__ int32_t table_collect(unsigned long long *tab, int32_
     }
     run += total;
   }
+  *used = T;
   if (sort && run > 0) {
     __syncthreads();  // compaction writes done
-    int32_t used;
-    *sorted_at = sort_survivors<NT>(tab, run, &used);
+    int32_t u;
+    *sorted_at = sort_survivors<NT>(tab, run, &u);
+    *used = max(T, u);
   }
   return run;
+}
+
+// Marks tab[0, n) free with 16-byte stores (tab is 16-byte aligned; an odd n
+// also clears slot n, which is free already or inside the region in use).
+template <int NT>
+__device__ __forceinline__ void clear_slots(unsigned long long *tab, int32_t n) {
+  ulonglong2 *t2 = reinterpret_cast<ulonglong2 *>(tab);
+  const ulonglong2 e = make_ulonglong2(kEmpty64, kEmpty64);
+  for (int32_t i = threadIdx.x; i < (n + 1) >> 1; i += NT) t2[i] = e;
 }
 
 // Survivors from the list: read their (f, count) slots, clear the whole
@@ -361,7 +432,7 @@ __device__ __forceinline__ int32_t table_collect_list(unsigned long long *tab, i
     x[q] = (sort && i < n) ? tab[sl.slot[i]] + 1ull : 0ull;  // count word holds count - 1
   }
   __syncthreads();  // reads done before the table is cleared
-  for (int32_t i = threadIdx.x; i < T; i += NT) tab[i] = kEmpty64;
+  clear_slots<NT>(tab, T);
   if (threadIdx.x == 0) *sl.n = 0;
   __syncthreads();
   *used = 0;
@@ -381,7 +452,7 @@ __device__ __forceinline__ int32_t table_collect_list(unsigned long long *tab, i
 template <int NT>
 __device__ __forceinline__ void table_reset_front(unsigned long long *tab, int32_t used) {
   __syncthreads();  // sorted entries may still be read
-  for (int32_t i = threadIdx.x; i < used; i += NT) tab[i] = kEmpty64;
+  clear_slots<NT>(tab, used);
   __syncthreads();
 }
 
@@ -439,8 +510,7 @@ __global__ __launch_bounds__(NT, MINB) void k_walk_cta(Walk w, const int32_t *__
       cta_walk<NT, 4>(w, k0, k1, s_beg, s_pref, ws, [&](int32_t f, int32_t) {
         table_insert<false>(tab, lgT, f, 1, smin, unweighted, meta, sl);
       });
-      total = table_collect<NT, Cfg::kSPT>(tab, T, smin, emit, ws, &at);
-      used = T;
+      total = table_collect<NT, Cfg::kSPT>(tab, T, smin, emit, ws, &at, &used);
     }
     if (threadIdx.x == 0) *s_base = reserve(a, e, total, BIN);
     __syncthreads();
@@ -810,7 +880,7 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
         } else {
           insert_all(std::false_type{});
           __syncthreads();
-          total = table_collect<kGiantNT, kGiantSPT>(tab, T, smin, emit, ws, &at);
+          total = table_collect<kGiantNT, kGiantSPT>(tab, T, smin, emit, ws, &at, &used);
         }
         if (a.mode == kStage && out + total > q4) {
           // staged pairs would not fit the scratch (sized by wedges + core

@@ -44,6 +44,17 @@ def test_binding_covers_every_declared_symbol():
     assert set(declared_functions()) == set(slg.ABI_FUNCTIONS)
 
 
+def test_binding_constants_match_header():
+    import paper_2010_11448_gb300 as slg
+    text = open(os.path.join(ROOT, "include", "slg.h")).read()
+    defs = dict(re.findall(r"^#define (SLG_\w+) (0x[0-9A-Fa-f]+|-?\d+)u?\b", text, flags=re.M))
+    defs.update(re.findall(r"^\s+(SLG_\w+) = (\d+),?", text, flags=re.M))  # slg_status
+    assert "SLG_ASYNC" in defs and "SLG_ERR_CAPACITY" in defs
+    for name, val in defs.items():
+        if hasattr(slg, name):
+            assert getattr(slg, name) == int(val, 0), name
+
+
 def test_host_only_calls(lib):
     import paper_2010_11448_gb300 as slg
     L = slg.load()

@@ -194,6 +194,34 @@ def test_host_entry_point_pinned(medium):
         assert ei.value.status == 2 and ei.value.needed == want.shape[0]
 
 
+def test_host_entry_point_async_streams(medium):
+    # SLG_ASYNC: four builds on four streams, each returning once its copies
+    # back are enqueued; after the streams complete every list is the oracle's
+    h, _ = medium
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).pin_memory()
+
+    class HostH:
+        pass
+    hh = HostH()
+    hh.m, hh.n = h.m, h.n
+    hh.e_off, hh.e_idx, hh.v_off, hh.v_idx = (pin(h.e_off), pin(h.e_idx), pin(h.v_off),
+                                              pin(h.v_idx))
+    jobs = [(False, 2), (True, 2), (False, 5), (True, 3)]
+    wants = [want_lg(h, s, dual) for dual, s in jobs]
+    streams = [torch.cuda.Stream() for _ in jobs]
+    for rep in range(2):
+        outs = [tuple(torch.full((w.shape[0] + 5,), -1, dtype=torch.int32).pin_memory()
+                      for _ in range(3)) for w in wants]
+        got = []
+        for (dual, s), o, st in zip(jobs, outs, streams):
+            got.append(slg.build_host(hh, s, dual=dual, out=o, stream=st, wait=False))
+        for st in streams:
+            st.synchronize()
+        for g, w, o in zip(got, wants, outs):
+            assert np.array_equal(np.stack([a.numpy() for a in g], 1).astype(np.int64), w)
+            assert int(o[0][w.shape[0]]) == -1
+
+
 def test_on_side_stream(medium):
     h, dh = medium
     st = torch.cuda.Stream()
