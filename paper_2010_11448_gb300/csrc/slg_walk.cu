@@ -570,6 +570,14 @@ constexpr int kGiantSPT = kGiantTMax / kGiantNT;
 constexpr int kDenseW = 2 * kGiantTMax;  // ids per dense window (int32 counters in the table)
 
 constexpr int kGiantList = kGiantTMax / 2;  // survivors of a bucket (<= its distinct keys)
+#ifndef SLG_GIANT_DIRECT_MAX
+#define SLG_GIANT_DIRECT_MAX 6144
+#endif
+// Rows of at most this many wedges skip the partition: one table, filled to
+// at most 3/4 (the survivor list holds work / 2 >= any s >= 2 survivor set).
+constexpr int32_t kGiantDirectMax = SLG_GIANT_DIRECT_MAX;
+static_assert(kGiantDirectMax <= kGiantTMax && kGiantDirectMax / 2 <= kGiantList,
+              "a direct row fits the table and the survivor list");
 constexpr int kGiantQ = kGiantList / kGiantNT;
 
 // [s_base 16][s_misc 16][table TMAX x 8][sub NSB][subt NSB+1][bstart NSB+1]
@@ -684,27 +692,6 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
       if (threadIdx.x == 0) raise_error(meta, SLG_ERR_INVALID, kWhereGiant);
       break;
     }
-    long long clk0 = clock64();
-    // 1. flattened far ends; a row within one super-chunk also counts its
-    // sub-range histogram here (saving one pass over the copy)
-    const bool single = R - f_lo <= chunk_w;
-    if (single) {
-      for (int i = threadIdx.x; i < kNSB; i += kGiantNT) {
-        sub[i] = 0;
-        subt[i] = 0;
-      }
-      __syncthreads();
-      cta_walk<kGiantNT, 4>(w, w.r_off[e], w.r_off[e + 1], s_beg, s_pref, ws,
-                            [&](int32_t f, int32_t i) {
-                              flat[i] = f;
-                              atomicAdd(sub + ((f - f_lo) >> shift), 1);
-                            });
-    } else {
-      cta_walk<kGiantNT, 4>(w, w.r_off[e], w.r_off[e + 1], s_beg, s_pref, ws,
-                            [&](int32_t f, int32_t i) { flat[i] = f; });
-    }
-    long long clk_part = 0, clk_bucket = 0;
-    if (threadIdx.x == 0) atomicAdd(&meta->giant_cycles[0], (unsigned long long)(clock64() - clk0));
     // Core rows also receive tile items (f, |e ∩ f ∩ C_c|) for every active
     // core row f > e with a non-zero tile count.
     const CoreInfo &ci = a.core;
@@ -714,202 +701,257 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
     long long base = -1;
     if (a.mode == kDirect) base = a.row_ptr[e - a.row_begin];
     int32_t out = 0;  // pairs of the row so far
-    for (int32_t F0 = f_lo; F0 < R; F0 += chunk_w) {
-      // An empty bucket is skipped without a barrier, so threads may still
-      // be reading the previous super-chunk's sub[] / bstart[] here: every
-      // thread must be done with them before they are rewritten.
-      __syncthreads();
-      const long long c0 = clock64();
-      const int32_t F1 = (R - F0 > chunk_w) ? F0 + chunk_w : R;
-      const int32_t nsb = ((F1 - F0 - 1) >> shift) + 1;
-      // 2. histograms of sub-ranges (wedges; tile items), scans, scatter
-      if (!single) {
+    if (work <= kGiantDirectMax && !core_row) {
+      // A row this small is counted in one table during the walk, as in the
+      // CTA bins (no flattened copy, no sub-ranges): its distinct far ends
+      // fill at most kGiantDirectMax / kGiantTMax of the table.
+      const int lgT = table_lg(work, lg_max);
+      const int32_t T = 1 << lgT;
+      int32_t at = 0, used = T;
+      if (smin >= 2) {
+        cta_walk<kGiantNT, 4>(w, w.r_off[e], w.r_off[e + 1], s_beg, s_pref, ws,
+                              [&](int32_t f, int32_t) {
+                                table_insert<true>(tab, lgT, f, 1, smin, unweighted, meta, sl);
+                              });
+        out = table_collect_list<kGiantNT, kGiantQ>(tab, T, sl, emit, &at, &used);
+      } else {
+        cta_walk<kGiantNT, 4>(w, w.r_off[e], w.r_off[e + 1], s_beg, s_pref, ws,
+                              [&](int32_t f, int32_t) {
+                                table_insert<false>(tab, lgT, f, 1, smin, unweighted, meta, sl);
+                              });
+        out = table_collect<kGiantNT, kGiantSPT>(tab, T, smin, emit, ws, &at, &used);
+      }
+      if (emit)
+        for (int32_t i = threadIdx.x; i < out; i += kGiantNT) {
+          const unsigned long long x = tab[at + i];
+          const int32_t f = (int32_t)(x >> 32), n = (int32_t)(uint32_t)x;
+          if (a.mode == kDirect) {
+            put(a, base, i, e, f, n);
+          } else {
+            tj[i] = f;
+            if (!unweighted) tw[i] = n;
+          }
+        }
+      table_reset_front<kGiantNT>(tab, used);
+    } else {
+      long long clk0 = clock64();
+      // 1. flattened far ends; a row within one super-chunk also counts its
+      // sub-range histogram here (saving one pass over the copy)
+      const bool single = R - f_lo <= chunk_w;
+      if (single) {
         for (int i = threadIdx.x; i < kNSB; i += kGiantNT) {
           sub[i] = 0;
           subt[i] = 0;
         }
         __syncthreads();
-        for_each_batched<kGiantNT, 8>(flat, 0, work, [&](int32_t f) {
-          if (f >= F0 && f < F1) atomicAdd(sub + ((f - F0) >> shift), 1);
-        });
+        cta_walk<kGiantNT, 4>(w, w.r_off[e], w.r_off[e + 1], s_beg, s_pref, ws,
+                              [&](int32_t f, int32_t i) {
+                                flat[i] = f;
+                                atomicAdd(sub + ((f - f_lo) >> shift), 1);
+                              });
+      } else {
+        cta_walk<kGiantNT, 4>(w, w.r_off[e], w.r_off[e + 1], s_beg, s_pref, ws,
+                              [&](int32_t f, int32_t i) { flat[i] = f; });
       }
-      if (core_row)
-        for (int32_t p = ri + 1 + (int32_t)threadIdx.x; p < ci.n_core; p += kGiantNT) {
-          const int32_t f = ci.core_list[p];
-          if (f >= F0 && f < F1 && w.r_off[f + 1] - w.r_off[f] >= smin && Trow[p] > 0)
-            atomicAdd(subt + ((f - F0) >> shift), 1);
-        }
-      __syncthreads();
-      const int32_t nw = scan_subranges(sub, ws);
-      const int32_t items = core_row ? scan_subranges(subt, ws) : 0;
-      if (nw == 0 && items == 0) continue;  // uniform: both totals are block-wide
-      if (threadIdx.x == 0) subt[kNSB] = items;
-      for_each_batched<kGiantNT, 8>(flat, 0, work, [&](int32_t f) {
-        if (f >= F0 && f < F1) wl[atomicAdd(sub + ((f - F0) >> shift), 1)] = f;
-      });
-      __syncthreads();
-      // now sub[b] = end of the wedges of sub-range b; subt[b] = start of its
-      // items.  3. bucket starts: sub-range b opens a bucket when its start
-      // in the merged order (wedges + items before it) / cap changes.
-      {
-        constexpr int P = kNSB / kGiantNT;
-        int32_t flag[P], t = 0;
-#pragma unroll
-        for (int q = 0; q < P; ++q) {
-          const int32_t b = threadIdx.x * P + q;
-          flag[q] = 0;
-          if (b < nsb) {
-            if (dense) {
-              flag[q] = ((b << shift) & (kDenseW - 1)) == 0;
-            } else {
-              const int32_t st = (b ? sub[b - 1] : 0) + (core_row ? subt[b] : 0);
-              const int32_t sp = b ? (b > 1 ? sub[b - 2] : 0) + (core_row ? subt[b - 1] : 0) : 0;
-              flag[q] = (b == 0) || (st / cap != sp / cap);
-            }
-          }
-          t += flag[q];
-        }
-        int32_t total;
-        const int32_t inc = block_inclusive_scan<kGiantNT>(t, ws, &total);
-        int32_t pos = inc - t;
-#pragma unroll
-        for (int q = 0; q < P; ++q)
-          if (flag[q]) bstart[pos++] = threadIdx.x * P + q;
-        if (threadIdx.x == 0) {
-          bstart[total] = nsb;
-          s_misc[1] = total;
-        }
+      long long clk_part = 0, clk_bucket = 0;
+      if (threadIdx.x == 0) atomicAdd(&meta->giant_cycles[0], (unsigned long long)(clock64() - clk0));
+      for (int32_t F0 = f_lo; F0 < R; F0 += chunk_w) {
+        // An empty bucket is skipped without a barrier, so threads may still
+        // be reading the previous super-chunk's sub[] / bstart[] here: every
+        // thread must be done with them before they are rewritten.
         __syncthreads();
-      }
-      const int32_t nb = s_misc[1];
-      const long long c1 = clock64();
-      clk_part += c1 - c0;
-      for (int32_t c = 0; c < nb; ++c) {
-        const int32_t b0 = bstart[c], b1 = bstart[c + 1];
-        const int32_t lo = b0 ? sub[b0 - 1] : 0, hi = sub[b1 - 1];
-        int32_t nit = 0;
-        if (core_row) {
-          nit = (b1 < nsb ? subt[b1] : subt[kNSB]) - subt[b0];
+        const long long c0 = clock64();
+        const int32_t F1 = (R - F0 > chunk_w) ? F0 + chunk_w : R;
+        const int32_t nsb = ((F1 - F0 - 1) >> shift) + 1;
+        // 2. histograms of sub-ranges (wedges; tile items), scans, scatter
+        if (!single) {
+          for (int i = threadIdx.x; i < kNSB; i += kGiantNT) {
+            sub[i] = 0;
+            subt[i] = 0;
+          }
+          __syncthreads();
+          for_each_batched<kGiantNT, 8>(flat, 0, work, [&](int32_t f) {
+            if (f >= F0 && f < F1) atomicAdd(sub + ((f - F0) >> shift), 1);
+          });
+        }
+        if (core_row)
+          for (int32_t p = ri + 1 + (int32_t)threadIdx.x; p < ci.n_core; p += kGiantNT) {
+            const int32_t f = ci.core_list[p];
+            if (f >= F0 && f < F1 && w.r_off[f + 1] - w.r_off[f] >= smin && Trow[p] > 0)
+              atomicAdd(subt + ((f - F0) >> shift), 1);
+          }
+        __syncthreads();
+        const int32_t nw = scan_subranges(sub, ws);
+        const int32_t items = core_row ? scan_subranges(subt, ws) : 0;
+        if (nw == 0 && items == 0) continue;  // uniform: both totals are block-wide
+        if (threadIdx.x == 0) subt[kNSB] = items;
+        for_each_batched<kGiantNT, 8>(flat, 0, work, [&](int32_t f) {
+          if (f >= F0 && f < F1) wl[atomicAdd(sub + ((f - F0) >> shift), 1)] = f;
+        });
+        __syncthreads();
+        // now sub[b] = end of the wedges of sub-range b; subt[b] = start of its
+        // items.  3. bucket starts: sub-range b opens a bucket when its start
+        // in the merged order (wedges + items before it) / cap changes.
+        {
+          constexpr int P = kNSB / kGiantNT;
+          int32_t flag[P], t = 0;
+  #pragma unroll
+          for (int q = 0; q < P; ++q) {
+            const int32_t b = threadIdx.x * P + q;
+            flag[q] = 0;
+            if (b < nsb) {
+              if (dense) {
+                flag[q] = ((b << shift) & (kDenseW - 1)) == 0;
+              } else {
+                const int32_t st = (b ? sub[b - 1] : 0) + (core_row ? subt[b] : 0);
+                const int32_t sp = b ? (b > 1 ? sub[b - 2] : 0) + (core_row ? subt[b - 1] : 0) : 0;
+                flag[q] = (b == 0) || (st / cap != sp / cap);
+              }
+            }
+            t += flag[q];
+          }
+          int32_t total;
+          const int32_t inc = block_inclusive_scan<kGiantNT>(t, ws, &total);
+          int32_t pos = inc - t;
+  #pragma unroll
+          for (int q = 0; q < P; ++q)
+            if (flag[q]) bstart[pos++] = threadIdx.x * P + q;
           if (threadIdx.x == 0) {
-            // core positions of the bucket's id range, after row e itself
-            const int32_t flo = F0 + (b0 << shift);
-            const int32_t fhi = b1 < nsb ? F0 + (b1 << shift) : F1;
-            s_misc[2] = max(core_lower(ci.core_list, ci.n_core, flo), ri + 1);
-            s_misc[3] = core_lower(ci.core_list, ci.n_core, fhi);
+            bstart[total] = nsb;
+            s_misc[1] = total;
           }
           __syncthreads();
         }
-        if (hi - lo + nit == 0) continue;  // uniform
-        if (dense) {
-          const int32_t fb0 = F0 + (b0 << shift);
-          const int32_t dw = min((b1 - b0) << shift, F1 - fb0);  // <= kDenseW
-          int32_t *cnt = reinterpret_cast<int32_t *>(tab);
-          for (int32_t i = threadIdx.x; i < dw; i += kGiantNT) cnt[i] = 0;
-          __syncthreads();
-          for_each_batched<kGiantNT, 8>(wl, lo, hi,
-                                        [&](int32_t f) { atomicAdd(cnt + (f - fb0), 1); });
-          if (core_row && nit > 0)
-            for (int32_t p = s_misc[2] + (int32_t)threadIdx.x; p < s_misc[3]; p += kGiantNT) {
-              const int32_t f = ci.core_list[p];
-              const int32_t wt = Trow[p];
-              if (wt > 0 && w.r_off[f + 1] - w.r_off[f] >= smin) atomicAdd(cnt + (f - fb0), wt);
+        const int32_t nb = s_misc[1];
+        const long long c1 = clock64();
+        clk_part += c1 - c0;
+        for (int32_t c = 0; c < nb; ++c) {
+          const int32_t b0 = bstart[c], b1 = bstart[c + 1];
+          const int32_t lo = b0 ? sub[b0 - 1] : 0, hi = sub[b1 - 1];
+          int32_t nit = 0;
+          if (core_row) {
+            nit = (b1 < nsb ? subt[b1] : subt[kNSB]) - subt[b0];
+            if (threadIdx.x == 0) {
+              // core positions of the bucket's id range, after row e itself
+              const int32_t flo = F0 + (b0 << shift);
+              const int32_t fhi = b1 < nsb ? F0 + (b1 << shift) : F1;
+              s_misc[2] = max(core_lower(ci.core_list, ci.n_core, flo), ri + 1);
+              s_misc[3] = core_lower(ci.core_list, ci.n_core, fhi);
             }
-          __syncthreads();
-          // ordered emission: warp q owns counters [q * span_w, (q + 1) * span_w)
-          const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
-          constexpr int NWq = kGiantNT / 32;
-          const int32_t span_w = ((dw + NWq - 1) / NWq + 31) & ~31;
-          const int32_t q0 = wq * span_w, q1 = min(dw, q0 + span_w);
-          int32_t c = 0;
-          for (int32_t i = q0 + lane; i < q1; i += 32) c += cnt[i] >= smin;
-#pragma unroll
-          for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
-          int32_t total;
-          const int32_t winc = block_inclusive_scan<kGiantNT>(lane == 0 ? c : 0, ws, &total);
-          int32_t pos = out + __shfl_sync(0xffffffffu, winc, 0) - c;  // warp's first slot
+            __syncthreads();
+          }
+          if (hi - lo + nit == 0) continue;  // uniform
+          if (dense) {
+            const int32_t fb0 = F0 + (b0 << shift);
+            const int32_t dw = min((b1 - b0) << shift, F1 - fb0);  // <= kDenseW
+            int32_t *cnt = reinterpret_cast<int32_t *>(tab);
+            for (int32_t i = threadIdx.x; i < dw; i += kGiantNT) cnt[i] = 0;
+            __syncthreads();
+            for_each_batched<kGiantNT, 8>(wl, lo, hi,
+                                          [&](int32_t f) { atomicAdd(cnt + (f - fb0), 1); });
+            if (core_row && nit > 0)
+              for (int32_t p = s_misc[2] + (int32_t)threadIdx.x; p < s_misc[3]; p += kGiantNT) {
+                const int32_t f = ci.core_list[p];
+                const int32_t wt = Trow[p];
+                if (wt > 0 && w.r_off[f + 1] - w.r_off[f] >= smin) atomicAdd(cnt + (f - fb0), wt);
+              }
+            __syncthreads();
+            // ordered emission: warp q owns counters [q * span_w, (q + 1) * span_w)
+            const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+            constexpr int NWq = kGiantNT / 32;
+            const int32_t span_w = ((dw + NWq - 1) / NWq + 31) & ~31;
+            const int32_t q0 = wq * span_w, q1 = min(dw, q0 + span_w);
+            int32_t c = 0;
+            for (int32_t i = q0 + lane; i < q1; i += 32) c += cnt[i] >= smin;
+  #pragma unroll
+            for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+            int32_t total;
+            const int32_t winc = block_inclusive_scan<kGiantNT>(lane == 0 ? c : 0, ws, &total);
+            int32_t pos = out + __shfl_sync(0xffffffffu, winc, 0) - c;  // warp's first slot
+            if (a.mode == kStage && out + total > q4) {
+              if (threadIdx.x == 0) raise_error(meta, SLG_ERR_INVALID, kWhereGiant);
+              break;
+            }
+            if (emit && total > 0) {
+              for (int32_t i0 = q0; i0 < q1; i0 += 32) {
+                const int32_t i = i0 + lane;
+                const int32_t n = i < q1 ? cnt[i] : 0;
+                const bool keep = i < q1 && n >= smin;
+                const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                if (keep) {
+                  const int32_t t = pos + __popc(bal & ((1u << lane) - 1));
+                  if (a.mode == kDirect) {
+                    put(a, base, t, e, fb0 + i, n);
+                  } else {
+                    tj[t] = fb0 + i;
+                    if (!unweighted) tw[t] = n;
+                  }
+                }
+                pos += __popc(bal);
+              }
+            }
+            out += total;
+            __syncthreads();
+            for (int32_t i = threadIdx.x; i < (dw + 1) / 2; i += kGiantNT) tab[i] = kEmpty64;
+            __syncthreads();
+            continue;
+          }
+          const int32_t width = (b1 - b0) << shift;
+          const int lgT = table_lg(min(hi - lo + nit, width), lg_max);
+          const int32_t T = 1 << lgT;
+          // s >= 2: survivors listed as they appear; s = 1: every key survives
+          const bool list = smin >= 2;
+          auto insert_all = [&](auto list_tag) {
+            constexpr bool L = decltype(list_tag)::value;
+            for_each_batched<kGiantNT, 8>(wl, lo, hi, [&](int32_t f) {
+              table_insert<L>(tab, lgT, f, 1, smin, unweighted, meta, sl);
+            });
+            if (core_row && nit > 0)
+              for (int32_t p = s_misc[2] + (int32_t)threadIdx.x; p < s_misc[3]; p += kGiantNT) {
+                const int32_t f = ci.core_list[p];
+                const int32_t wt = Trow[p];
+                if (wt > 0 && w.r_off[f + 1] - w.r_off[f] >= smin)
+                  table_insert<L>(tab, lgT, f, wt, smin, unweighted, meta, sl);
+              }
+          };
+          int32_t at = 0, used = T, total;
+          if (list) {
+            insert_all(std::true_type{});
+            total = table_collect_list<kGiantNT, kGiantQ>(tab, T, sl, emit, &at, &used);
+          } else {
+            insert_all(std::false_type{});
+            __syncthreads();
+            total = table_collect<kGiantNT, kGiantSPT>(tab, T, smin, emit, ws, &at, &used);
+          }
           if (a.mode == kStage && out + total > q4) {
+            // staged pairs would not fit the scratch (sized by wedges + core
+            // items): report instead of writing past it
             if (threadIdx.x == 0) raise_error(meta, SLG_ERR_INVALID, kWhereGiant);
+            table_reset_front<kGiantNT>(tab, used);
             break;
           }
           if (emit && total > 0) {
-            for (int32_t i0 = q0; i0 < q1; i0 += 32) {
-              const int32_t i = i0 + lane;
-              const int32_t n = i < q1 ? cnt[i] : 0;
-              const bool keep = i < q1 && n >= smin;
-              const unsigned bal = __ballot_sync(0xffffffffu, keep);
-              if (keep) {
-                const int32_t t = pos + __popc(bal & ((1u << lane) - 1));
-                if (a.mode == kDirect) {
-                  put(a, base, t, e, fb0 + i, n);
-                } else {
-                  tj[t] = fb0 + i;
-                  if (!unweighted) tw[t] = n;
-                }
+            for (int32_t i = threadIdx.x; i < total; i += kGiantNT) {
+              const unsigned long long x = tab[at + i];
+              const int32_t f = (int32_t)(x >> 32), n = (int32_t)(uint32_t)x;
+              if (a.mode == kDirect) {
+                put(a, base, out + i, e, f, n);
+              } else {
+                tj[out + i] = f;
+                if (!unweighted) tw[out + i] = n;
               }
-              pos += __popc(bal);
             }
           }
           out += total;
-          __syncthreads();
-          for (int32_t i = threadIdx.x; i < (dw + 1) / 2; i += kGiantNT) tab[i] = kEmpty64;
-          __syncthreads();
-          continue;
-        }
-        const int32_t width = (b1 - b0) << shift;
-        const int lgT = table_lg(min(hi - lo + nit, width), lg_max);
-        const int32_t T = 1 << lgT;
-        // s >= 2: survivors listed as they appear; s = 1: every key survives
-        const bool list = smin >= 2;
-        auto insert_all = [&](auto list_tag) {
-          constexpr bool L = decltype(list_tag)::value;
-          for_each_batched<kGiantNT, 8>(wl, lo, hi, [&](int32_t f) {
-            table_insert<L>(tab, lgT, f, 1, smin, unweighted, meta, sl);
-          });
-          if (core_row && nit > 0)
-            for (int32_t p = s_misc[2] + (int32_t)threadIdx.x; p < s_misc[3]; p += kGiantNT) {
-              const int32_t f = ci.core_list[p];
-              const int32_t wt = Trow[p];
-              if (wt > 0 && w.r_off[f + 1] - w.r_off[f] >= smin)
-                table_insert<L>(tab, lgT, f, wt, smin, unweighted, meta, sl);
-            }
-        };
-        int32_t at = 0, used = T, total;
-        if (list) {
-          insert_all(std::true_type{});
-          total = table_collect_list<kGiantNT, kGiantQ>(tab, T, sl, emit, &at, &used);
-        } else {
-          insert_all(std::false_type{});
-          __syncthreads();
-          total = table_collect<kGiantNT, kGiantSPT>(tab, T, smin, emit, ws, &at, &used);
-        }
-        if (a.mode == kStage && out + total > q4) {
-          // staged pairs would not fit the scratch (sized by wedges + core
-          // items): report instead of writing past it
-          if (threadIdx.x == 0) raise_error(meta, SLG_ERR_INVALID, kWhereGiant);
           table_reset_front<kGiantNT>(tab, used);
-          break;
         }
-        if (emit && total > 0) {
-          for (int32_t i = threadIdx.x; i < total; i += kGiantNT) {
-            const unsigned long long x = tab[at + i];
-            const int32_t f = (int32_t)(x >> 32), n = (int32_t)(uint32_t)x;
-            if (a.mode == kDirect) {
-              put(a, base, out + i, e, f, n);
-            } else {
-              tj[out + i] = f;
-              if (!unweighted) tw[out + i] = n;
-            }
-          }
-        }
-        out += total;
-        table_reset_front<kGiantNT>(tab, used);
+        clk_bucket += clock64() - c1;
       }
-      clk_bucket += clock64() - c1;
-    }
-    if (threadIdx.x == 0) {
-      atomicAdd(&meta->giant_cycles[1], (unsigned long long)clk_part);
-      atomicAdd(&meta->giant_cycles[2], (unsigned long long)clk_bucket);
-    }
+      if (threadIdx.x == 0) {
+        atomicAdd(&meta->giant_cycles[1], (unsigned long long)clk_part);
+        atomicAdd(&meta->giant_cycles[2], (unsigned long long)clk_bucket);
+      }
+    }  // partitioned row
     if (threadIdx.x == 0) *s_base = reserve(a, e, out, kBinGiant);
     __syncthreads();
     if (a.mode == kStage) {
