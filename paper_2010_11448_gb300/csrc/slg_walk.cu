@@ -576,6 +576,7 @@ constexpr int kGiantList = kGiantTMax / 2;  // survivors of a bucket (<= its dis
 // Rows of at most this many wedges skip the partition: one table, filled to
 // at most 3/4 (the survivor list holds work / 2 >= any s >= 2 survivor set).
 constexpr int32_t kGiantDirectMax = SLG_GIANT_DIRECT_MAX;
+constexpr int kGiantG = 6;  // wedges per thread per step of the giant bin's walk (4, 6, 8 swept)
 static_assert(kGiantDirectMax <= kGiantTMax && kGiantDirectMax / 2 <= kGiantList,
               "a direct row fits the table and the survivor list");
 constexpr int kGiantQ = kGiantList / kGiantNT;
@@ -709,13 +710,13 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
       const int32_t T = 1 << lgT;
       int32_t at = 0, used = T;
       if (smin >= 2) {
-        cta_walk<kGiantNT, 4>(w, w.r_off[e], w.r_off[e + 1], s_beg, s_pref, ws,
+        cta_walk<kGiantNT, kGiantG>(w, w.r_off[e], w.r_off[e + 1], s_beg, s_pref, ws,
                               [&](int32_t f, int32_t) {
                                 table_insert<true>(tab, lgT, f, 1, smin, unweighted, meta, sl);
                               });
         out = table_collect_list<kGiantNT, kGiantQ>(tab, T, sl, emit, &at, &used);
       } else {
-        cta_walk<kGiantNT, 4>(w, w.r_off[e], w.r_off[e + 1], s_beg, s_pref, ws,
+        cta_walk<kGiantNT, kGiantG>(w, w.r_off[e], w.r_off[e + 1], s_beg, s_pref, ws,
                               [&](int32_t f, int32_t) {
                                 table_insert<false>(tab, lgT, f, 1, smin, unweighted, meta, sl);
                               });
@@ -744,13 +745,13 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
           subt[i] = 0;
         }
         __syncthreads();
-        cta_walk<kGiantNT, 4>(w, w.r_off[e], w.r_off[e + 1], s_beg, s_pref, ws,
+        cta_walk<kGiantNT, kGiantG>(w, w.r_off[e], w.r_off[e + 1], s_beg, s_pref, ws,
                               [&](int32_t f, int32_t i) {
                                 flat[i] = f;
                                 atomicAdd(sub + ((f - f_lo) >> shift), 1);
                               });
       } else {
-        cta_walk<kGiantNT, 4>(w, w.r_off[e], w.r_off[e + 1], s_beg, s_pref, ws,
+        cta_walk<kGiantNT, kGiantG>(w, w.r_off[e], w.r_off[e + 1], s_beg, s_pref, ws,
                               [&](int32_t f, int32_t i) { flat[i] = f; });
       }
       long long clk_part = 0, clk_bucket = 0;
