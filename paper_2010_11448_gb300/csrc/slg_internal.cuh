@@ -28,6 +28,12 @@ enum Bin : int { kBinWarp = 0, kBinCtaS = 1, kBinCtaL = 2, kBinGiant = 3, kNumBi
 constexpr int32_t kWarpMaxWork = 128;
 constexpr int32_t kCtaSMaxWork = 1024;
 constexpr int32_t kCtaLMaxWork = 4096;
+// Giant rows above this work are handed out first (largest-first order
+// bounds the tail of the dynamic schedule by the largest remaining row).
+#ifndef SLG_GIANT_HUGE_WORK
+#define SLG_GIANT_HUGE_WORK 32768
+#endif
+constexpr int32_t kGiantHugeWork = SLG_GIANT_HUGE_WORK;
 
 // Counters the device writes and the host reads once per call.
 struct Meta {
@@ -43,6 +49,8 @@ struct Meta {
   unsigned long long stage_cursor;     // staging allocator
   unsigned long long stage_overflow;   // rows that did not fit the staging
   unsigned int giant_ticket;           // dynamic giant-row scheduling
+  unsigned int giant_huge;             // giant rows above kGiantHugeWork (front of the list)
+  unsigned int giant_rest;             // the other giant rows (back of the list)
   int32_t kept;                        // entries of the filtered CSC
   int32_t max_giant_work;              // largest work of a giant-bin row
   unsigned long long nnz_core;         // incidences of the dense core

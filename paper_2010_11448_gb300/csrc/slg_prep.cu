@@ -192,6 +192,7 @@ __global__ __launch_bounds__(kRowsNT) void k_rows_work(Side s, int32_t smin, int
   if (meta->err) return;
   __shared__ int32_t s_work[kRowsPerBlock];
   __shared__ int32_t s_cnt[kNumBins], s_base[kNumBins];
+  __shared__ int32_t s_hcnt, s_hbase;  // giant rows above kGiantHugeWork
   __shared__ unsigned long long s_w[kNumBins], s_k[kNumBins];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int32_t r0 = row_begin + blockIdx.x * kRowsPerBlock;
@@ -200,6 +201,7 @@ __global__ __launch_bounds__(kRowsNT) void k_rows_work(Side s, int32_t smin, int
     s_w[threadIdx.x] = 0;
     s_k[threadIdx.x] = 0;
   }
+  if (threadIdx.x == 0) s_hcnt = 0;
   for (int i = warp; i < kRowsPerBlock; i += kRowsNT / 32) {
     const int32_t e = r0 + i;
     int32_t work = 0;
@@ -250,6 +252,7 @@ __global__ __launch_bounds__(kRowsNT) void k_rows_work(Side s, int32_t smin, int
   }
   __syncthreads();
   int my_bin = -1, my_slot = 0;
+  bool huge = false;
   int32_t my_work = 0;
   if (threadIdx.x < kRowsPerBlock) {
     my_work = s_work[threadIdx.x];
@@ -258,7 +261,8 @@ __global__ __launch_bounds__(kRowsNT) void k_rows_work(Side s, int32_t smin, int
     if (my_work > 0 || forced) {
       my_bin = forced ? (int)kBinGiant : bin_of(my_work, bins);
       if (my_bin == kBinGiant) atomicMax(&meta->max_giant_work, my_work);
-      my_slot = atomicAdd(&s_cnt[my_bin], 1);
+      huge = my_bin == kBinGiant && my_work > kGiantHugeWork;
+      my_slot = huge ? atomicAdd(&s_hcnt, 1) : atomicAdd(&s_cnt[my_bin], 1);
       atomicAdd(&s_w[my_bin], (unsigned long long)my_work);
       const int32_t e = r0 + threadIdx.x;
       atomicAdd(&s_k[my_bin], (unsigned long long)(s.r_off[e + 1] - s.r_off[e]));
@@ -267,7 +271,17 @@ __global__ __launch_bounds__(kRowsNT) void k_rows_work(Side s, int32_t smin, int
   __syncthreads();
   if (threadIdx.x < kNumBins) {
     const int b = threadIdx.x;
-    s_base[b] = s_cnt[b] ? (int32_t)atomicAdd(&meta->rows_bin[b], (unsigned long long)s_cnt[b]) : 0;
+    if (b != kBinGiant) {
+      s_base[b] = s_cnt[b] ? (int32_t)atomicAdd(&meta->rows_bin[b], (unsigned long long)s_cnt[b]) : 0;
+    } else {
+      // the giant bin's huge rows fill its list from the front, the others
+      // from the back (k_walk_giant hands out the huge ones first); rows_bin
+      // counts both
+      if (s_cnt[b] + s_hcnt)
+        atomicAdd(&meta->rows_bin[b], (unsigned long long)(s_cnt[b] + s_hcnt));
+      s_base[b] = s_cnt[b] ? (int32_t)atomicAdd(&meta->giant_rest, (unsigned)s_cnt[b]) : 0;
+      s_hbase = s_hcnt ? (int32_t)atomicAdd(&meta->giant_huge, (unsigned)s_hcnt) : 0;
+    }
     if (s_w[b]) {
       atomicAdd(&meta->wedges_bin[b], s_w[b]);
       atomicAdd(&meta->wedges, s_w[b]);
@@ -283,8 +297,13 @@ __global__ __launch_bounds__(kRowsNT) void k_rows_work(Side s, int32_t smin, int
     if (act) atomicAdd(&meta->active, (unsigned long long)act);
   }
   __syncthreads();
-  if (my_bin >= 0) bin_rows[(int64_t)my_bin * (row_end - row_begin) + s_base[my_bin] + my_slot] =
-      r0 + threadIdx.x;
+  if (my_bin >= 0) {
+    const int64_t len = row_end - row_begin;
+    int64_t pos = s_base[my_bin] + my_slot;
+    if (huge) pos = s_hbase + my_slot;
+    else if (my_bin == kBinGiant) pos = len - 1 - pos;
+    bin_rows[(int64_t)my_bin * len + pos] = r0 + threadIdx.x;
+  }
 }
 
 inline int grid_for(int64_t items, int per_block, int cap = 1 << 20) {

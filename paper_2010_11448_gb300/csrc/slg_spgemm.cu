@@ -78,8 +78,13 @@ __global__ __launch_bounds__(kNT) void k_rows_full(Side s, int32_t row_begin, in
     s_base[threadIdx.x] =
         (int32_t)atomicAdd(&meta->rows_bin[threadIdx.x], (unsigned long long)s_cnt[threadIdx.x]);
   __syncthreads();
-  if (my_bin >= 0)
-    bin_rows[(int64_t)my_bin * list_stride + s_base[my_bin] + my_slot] = r0 + threadIdx.x;
+  if (my_bin >= 0) {
+    // giant rows fill their list from the back: k_walk_giant hands out the
+    // rows at its front (none here) first, then the back ones
+    int64_t pos = s_base[my_bin] + my_slot;
+    if (my_bin == kBinGiant) pos = list_stride - 1 - pos;
+    bin_rows[(int64_t)my_bin * list_stride + pos] = r0 + threadIdx.x;
+  }
 }
 
 // Filtration, count: entries of product row e with j > e and value >= s.

@@ -527,9 +527,12 @@ __global__ __launch_bounds__(NT, MINB) void k_walk_cta(Walk w, const int32_t *__
 
 // ------------------------------------------------------------- giant bin --
 //
-// A CTA takes one giant row at a time (dynamic ticket); two CTAs share an
-// SM.  The row's far ends f lie in [f_lo, R) (f_lo = e + 1 for the
-// upper-triangle walk, 0 for whole columns).
+// A CTA takes one giant row at a time (dynamic ticket; rows above
+// kGiantHugeWork wedges first, so that the schedule ends on small rows); two
+// CTAs share an SM.  The row's far ends f lie in [f_lo, R) (f_lo = e + 1 for
+// the upper-triangle walk, 0 for whole columns).  Rows of at most
+// kGiantDirectMax wedges are counted in one table during the walk; the
+// others are partitioned:
 //   1. one load-balanced walk copies the row's far ends, in flattened wedge
 //      order, to the CTA's global scratch `flat` (coalesced stores); a row
 //      whose ids fit one super-chunk also counts its sub-range histogram
@@ -642,7 +645,8 @@ __device__ __forceinline__ int32_t core_lower(const int32_t *core_list, int32_t 
 
 __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w, const int32_t *__restrict__ rows,
                                                             EmitArgs a, int32_t *__restrict__ scratch,
-                                                            long long scratch_stride, int32_t R) {
+                                                            long long scratch_stride, int32_t R,
+                                                            int32_t list_len) {
   Meta *meta = a.meta;
   if (meta->err) return;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -667,6 +671,7 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
   for (int i = threadIdx.x; i < kGiantTMax; i += kGiantNT) tab[i] = kEmpty64;
   if (threadIdx.x == 0) *sl.n = 0;
   const unsigned nrows = (unsigned)meta->rows_bin[kBinGiant];
+  const unsigned nhuge = meta->giant_huge;  // rows[0, nhuge); the others end at rows[list_len)
   const bool unweighted = a.unweighted != 0;
   const bool emit = a.mode != kCount;
   constexpr int lg_max = 31 - __builtin_clz(kGiantTMax);
@@ -674,7 +679,7 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
     __syncthreads();
     if (threadIdx.x == 0) {
       const unsigned t = atomicAdd(&meta->giant_ticket, 1u);
-      s_misc[0] = t < nrows ? rows[t] : -1;
+      s_misc[0] = t >= nrows ? -1 : rows[t < nhuge ? t : list_len - 1 - (t - nhuge)];
     }
     __syncthreads();
     const int32_t e = s_misc[0];
@@ -1034,7 +1039,7 @@ cudaError_t launch_walk(const WalkLaunch &L, cudaStream_t st, int32_t *launches,
   if (ev) cudaEventRecord(ev[3], st);
   if (L.giant_scratch) {
     k_walk_giant<<<o.sms * o.g_blocks, kGiantNT, giant_smem(), st>>>(
-        L.w, lists + 3 * stride, L.a, L.giant_scratch, L.giant_stride, L.R);
+        L.w, lists + 3 * stride, L.a, L.giant_scratch, L.giant_stride, L.R, (int32_t)stride);
     ++n;
   }
   if (ev) cudaEventRecord(ev[4], st);
