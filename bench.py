@@ -885,6 +885,9 @@ def run_table(args):
                 count_ms = (time.perf_counter() - t0) * 1e3
                 _, n1, _, idx1 = oracle.side(h, dual)
                 d = np.bincount(idx1, minlength=n1).astype(np.int64)
+                for _ in slg.build_stream(dh, 1, 400_000_000, dual=dual):
+                    pass  # untimed warm-up pass
+                torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 tp, tw, chunks = 0, 0, 0
                 for _, _, i1, _, w1 in slg.build_stream(dh, 1, 400_000_000, dual=dual):
