@@ -65,6 +65,24 @@ def test_host_only_calls(lib):
     assert L.slg_count(None, 2, 0, ctypes.byref(n), None) == 1
 
 
+def test_async_flag_only_for_host_builds(lib):
+    # flag checks run on the host before any device work: SLG_ASYNC is
+    # accepted by slg_build_host alone (the others reject it as invalid)
+    import paper_2010_11448_gb300 as slg
+    L = slg.load()
+    dummy = ctypes.c_void_p(16)  # never dereferenced: the calls stop at the flag check
+    h = slg._Hypergraph(3, 4, 5, dummy, dummy, dummy, dummy)
+    n = ctypes.c_int64(0)
+    assert L.slg_count(ctypes.byref(h), 2, slg.SLG_ASYNC, ctypes.byref(n), None) == 1
+    assert L.slg_build(ctypes.byref(h), 2, slg.SLG_ASYNC, None, None, None, 0,
+                       ctypes.byref(n), None) == 1
+    # with SLG_ASYNC the host entry point still checks its own arguments
+    assert L.slg_build_host(ctypes.byref(h), 0, slg.SLG_ASYNC, None, None, None, 0,
+                            ctypes.byref(n), None) == 1  # s < 1
+    assert L.slg_build_host(ctypes.byref(h), 2, slg.SLG_ASYNC | 0x80, None, None, None, 0,
+                            ctypes.byref(n), None) == 1  # unknown flag
+
+
 def test_missing_library_fails_loudly(tmp_path):
     import paper_2010_11448_gb300 as slg
     with pytest.raises(RuntimeError):
