@@ -48,6 +48,9 @@ class Hypergraph:
     v_off: np.ndarray      # int32[n+1]
     v_idx: np.ndarray      # int32[nnz], rows ascending
     name: str = ""
+    # planted dense core (lognormal_web): its hyperedge and vertex ids, else None
+    core_edges: np.ndarray | None = None
+    core_vertices: np.ndarray | None = None
 
     @property
     def nnz(self) -> int:
@@ -56,7 +59,8 @@ class Hypergraph:
     def dual(self) -> "Hypergraph":
         """H*: vertices become hyperedges and vice versa (arrays swapped)."""
         return Hypergraph(self.n, self.m, self.v_off, self.v_idx,
-                          self.e_off, self.e_idx, self.name + "*")
+                          self.e_off, self.e_idx, self.name + "*",
+                          self.core_vertices, self.core_edges)
 
     def side(self, dual: bool) -> "Hypergraph":
         return self.dual() if dual else self
@@ -237,6 +241,7 @@ def lognormal_web(m: int, n: int, seed: int, mu: float = 2.0,
     sizes = np.clip(np.rint(rng.lognormal(mu, sigma, size=m)), 1, cap)
     sizes = np.minimum(sizes.astype(np.int64), n)
     r, c = _draw_distinct(sizes, n, rng, None)
+    ce = cv = None
     if core_edges > 0 and core_vertices > 0 and core_density > 0:
         ce = rng.choice(m, size=min(core_edges, m), replace=False)
         cv = rng.choice(n, size=min(core_vertices, n), replace=False)
@@ -244,7 +249,11 @@ def lognormal_web(m: int, n: int, seed: int, mu: float = 2.0,
         ri, ci = np.nonzero(hit)
         r = np.concatenate([r, ce[ri].astype(np.int64)])
         c = np.concatenate([c, cv[ci].astype(np.int64)])
-    return from_pairs(r, c, m, n, name)
+    h = from_pairs(r, c, m, n, name)
+    if ce is not None:
+        h.core_edges = np.sort(ce).astype(np.int32)
+        h.core_vertices = np.sort(cv).astype(np.int32)
+    return h
 
 
 def _batch_member(args):

@@ -358,13 +358,18 @@ int slg_plan_destroy(slg_plan *plan);
  *    H, or vertices with SLG_DUAL).  Larger inputs return SLG_ERR_TOO_LARGE
  *    without any device work.
  *  - The first call on a device looks up the array's device address (once
- *    per device); make that first call before any stream capture.
- *  - Every call shares the array and keeps the previous call's contents;
- *    each call clears the part it uses at its start.  Calls whose work
- *    overlaps on the GPU (other streams, other host threads) race on the
- *    array: do not let them overlap.
- *  - The input is checked on the device (offsets, id ranges, ascending
- *    rows) but, unlike slg_count, not cross-checked between CSR and CSC.
+ *    per device); make that first call before any stream capture begins.
+ *  - The call returns only once the count has reached the host: it waits
+ *    for its stream.
+ *  - Every call shares the array and keeps the previous call's contents.
+ *    The result block is cleared at the start of every call; the counters
+ *    and bitmaps are cleared too when the previous call on the device
+ *    stopped with an error (a call that completes leaves them zero).  Calls
+ *    whose work overlaps on the GPU (other streams, other host threads) race
+ *    on the array: do not let them overlap.
+ *  - The input is checked on the device as slg_count checks it: offsets, id
+ *    ranges, strictly ascending rows and columns, and CSR and CSC describing
+ *    the same incidence (SLG_ERR_INVALID otherwise).
  *  - It runs the plain per-hyperedge kernel (one warp per hyperedge), so it
  *    is slower than slg_count.
  */

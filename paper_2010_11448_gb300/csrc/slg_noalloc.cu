@@ -28,6 +28,12 @@ static __device__ __align__(256) int32_t g_noalloc_scratch[kNoallocInts];
 struct NoallocDevice {
   int32_t *base = nullptr;  // device address of g_noalloc_scratch
   bool ready = false;
+  // Set when a call may have left non-zero counters or bitmap words behind
+  // (it returned with an error after its memset).  A call that completes
+  // sets every counter and bitmap word it touched back to zero, and the
+  // array is zero when the library is loaded, so only then does the next
+  // call clear more than the result block.
+  bool dirty = false;
 };
 
 std::mutex g_noalloc_mu;
@@ -92,14 +98,38 @@ __global__ __launch_bounds__(kNoallocNT) void k_noalloc_count(Side sd, int32_t s
   if (lane == 0 && pairs) atomicAdd(&meta->pairs, pairs);
 }
 
+// CSR and CSC must describe the same incidence: one warp per CSR row e
+// looks e up in the (validated, ascending) column of each of its vertices.
+// With nnz equal on both sides and strictly ascending rows and columns, a
+// hit for every CSR incidence means the two are the same set.  Needs no
+// memory beyond the inputs; a miss raises SLG_ERR_INVALID.
+__global__ __launch_bounds__(kNoallocNT) void k_noalloc_agree(Side sd, Meta *meta) {
+  if (meta->err) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * kNoallocNT + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * kNoallocNT) >> 5;
+  for (int64_t e = gw; e < sd.R; e += nw) {
+    const int32_t lo = sd.r_off[e], hi = sd.r_off[e + 1];
+    bool miss = false;
+    for (int32_t k = lo + lane; k < hi; k += 32) {
+      const int32_t v = __ldg(sd.r_idx + k);
+      if (find_sorted(sd.c_idx, __ldg(sd.c_off + v), __ldg(sd.c_off + v + 1), (int32_t)e) < 0)
+        miss = true;
+    }
+    if (__any_sync(0xffffffffu, miss) && lane == 0)
+      raise_error(meta, SLG_ERR_INVALID, kWhereMismatch);
+  }
+}
+
 // Device address of the static array for the current device (first call per
 // device looks it up).
-cudaError_t noalloc_base(int32_t **out) {
+cudaError_t noalloc_base(int32_t **out, NoallocDevice **dv) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   NoallocDevice &d = g_noalloc_dev[dev % 64];
+  *dv = &d;
   if (!d.ready) {
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -146,7 +176,8 @@ extern "C" int slg_count_noalloc(const slg_hypergraph *h, int32_t s, uint32_t fl
 
   cudaStream_t st = (cudaStream_t)stream;
   int32_t *base = nullptr;
-  cudaError_t e = noalloc_base(&base);
+  NoallocDevice *dv = nullptr;
+  cudaError_t e = noalloc_base(&base, &dv);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return SLG_ERR_CUDA;
@@ -154,20 +185,29 @@ extern "C" int slg_count_noalloc(const slg_hypergraph *h, int32_t s, uint32_t fl
   Meta *meta = reinterpret_cast<Meta *>(base);
   int32_t *counters = base + kNoallocResultInts;
   uint32_t *bitmaps = reinterpret_cast<uint32_t *>(counters + warps * R_pad);
-  // What must start at zero: the result block, and the counters and bitmaps
-  // this call uses (a previous call that stopped early may have left them).
-  const size_t used = (size_t)(kNoallocResultInts + warps * R_pad + warps * (R_pad / 1024));
+  // What must start at zero: the result block always; the counters and
+  // bitmaps this call uses only after a call that may have stopped early.
+  bool clear_all;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    clear_all = dv->dirty;
+    dv->dirty = true;  // until this call has finished cleanly
+  }
+  const size_t used = clear_all ? (size_t)(kNoallocResultInts + warps * R_pad +
+                                           warps * (R_pad / 1024))
+                                : (size_t)kNoallocResultInts;
   if (cudaMemsetAsync(base, 0, used * sizeof(int32_t), st) != cudaSuccess) {
     cudaGetLastError();
     return SLG_ERR_CUDA;
   }
-  // Input checks on the device (offsets, id ranges, ascending rows) before
-  // the walk reads anything through them.
+  // Input checks on the device (offsets, id ranges, ascending rows, CSR and
+  // CSC the same incidence) before the walk reads anything through them.
   if (launch_validate(sd, meta, st) != cudaSuccess) {
     cudaGetLastError();
     return SLG_ERR_CUDA;
   }
   const int grid = (int)((warps * 32 + kNoallocNT - 1) / kNoallocNT);
+  k_noalloc_agree<<<grid, kNoallocNT, 0, st>>>(sd, meta);
   k_noalloc_count<<<grid, kNoallocNT, 0, st>>>(sd, s, counters, bitmaps, (int32_t)R_pad,
                                               (flags & SLG_UNWEIGHTED) ? 1 : 0, meta);
   if (cudaGetLastError() != cudaSuccess) return SLG_ERR_CUDA;
@@ -176,6 +216,11 @@ extern "C" int slg_count_noalloc(const slg_hypergraph *h, int32_t s, uint32_t fl
       cudaStreamSynchronize(st) != cudaSuccess) {
     cudaGetLastError();
     return SLG_ERR_CUDA;
+  }
+  if (!m.err) {
+    // the count kernel ran to the end: every counter it touched is zero again
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    dv->dirty = false;
   }
   if (m.err) return m.err;
   *n_pairs = (int64_t)m.pairs;

@@ -59,7 +59,8 @@ def test_unsupported(medium):
 
 def test_l1_full_size_streamed():
     # L_1 of the 1M x 2M Chung-Lu workload has 1.7e9 (H) and 7.8e9 (H*) pairs;
-    # streamed in chunks of at most 4e8 pairs, the weights add up to the
+    # streamed in chunks of at most 4e8 pairs: every 997th row of every chunk
+    # equals the oracle's element by element, the weights add up to the
     # closed form and the pair count matches slg_count
     c = dict(hg.CONFIGS["chung_lu_1m"])
     c.pop("kind")
@@ -69,10 +70,21 @@ def test_l1_full_size_streamed():
         m, n, off, idx = oracle.side(h, dual)
         d = np.bincount(idx, minlength=n).astype(np.int64)
         closed = int((d * (d - 1) // 2).sum())
+        rows = np.arange(0, m, 997, dtype=np.int32)
+        want = oracle.canonical(*oracle.line_graph(m, n, off, idx, 1, rows=rows, threads=16))
+        rows_t = torch.from_numpy(rows).cuda()
         total_w = 0
         total_p = 0
+        chunks = 0
+        got = []
         for a, b, i, j, w in slg.build_stream(dh, 1, 400_000_000, dual=dual):
+            chunks += 1
             total_p += int(i.shape[0])
             total_w += int(w.sum(dtype=torch.int64))
+            sel = torch.isin(i, rows_t)
+            got.append(np.stack([i[sel].cpu().numpy(), j[sel].cpu().numpy(),
+                                 w[sel].cpu().numpy()], 1).astype(np.int64))
+        assert chunks >= 4
+        assert np.array_equal(np.concatenate(got), want)
         assert total_w == closed
         assert total_p == slg.count(dh, 1, dual)
