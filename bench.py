@@ -198,7 +198,8 @@ def walk_bytes(st, b):
 
 
 WALK_KERNELS = ["k_walk_warp", "k_walk_cta<256,2048>", "k_walk_cta<256,8192>",
-                "k_walk_giant"]
+                "k_walk_giant", "k_walk_sparse"]
+NBINS = len(WALK_KERNELS)
 
 
 def recorded_traffic(kernel: str):
@@ -358,8 +359,8 @@ def run_ours(args):
     W_step = sum(wedges.values())
     P_step = sum(caps.values())
 
-    stats_acc = {"launches": 0, "ms_walk": [0.0] * 4, "bytes_walk": [0.0] * 4,
-                 "launch_walk": [0] * 4, "ms_other": 0.0}
+    stats_acc = {"launches": 0, "ms_walk": [0.0] * NBINS, "bytes_walk": [0.0] * NBINS,
+                 "launch_walk": [0] * NBINS, "ms_other": 0.0}
 
     def step(record):
         for dual, s in J:
@@ -368,7 +369,7 @@ def run_ours(args):
                 st = slg.last_stats()
                 stats_acc["launches"] += st["kernel_launches"]
                 if st["profiled"]:
-                    for b in range(4):
+                    for b in range(NBINS):
                         stats_acc["ms_walk"][b] += st["ms_walk"][b]
                         stats_acc["bytes_walk"][b] += walk_bytes(st, b)
                         stats_acc["launch_walk"][b] += 1
@@ -414,7 +415,7 @@ def run_ours(args):
                 "peak_source": peak_kind, "traffic": recorded_traffic(WALK_KERNELS[b]),
                 "algorithmic_bytes_per_launch": bytes_l, "ms_per_launch": t_l * 1e3,
                 "walk_ms_share": {WALK_KERNELS[i]: stats_acc["ms_walk"][i] / max(ms, 1e-9)
-                                  for i in range(4)}}
+                                  for i in range(NBINS)}}
 
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -936,7 +937,7 @@ def run_table(args):
                 slg.set_profiling(False)
                 W = st["wedges"]
                 walk_ms = sum(st["ms_walk"])
-                wbytes = sum(walk_bytes(st, b) for b in range(4))
+                wbytes = sum(walk_bytes(st, b) for b in range(NBINS))
                 if cname == "uniform_2k":
                     rows = None
                     sel = res

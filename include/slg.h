@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define SLG_ABI_VERSION 1
+#define SLG_ABI_VERSION 2
 
 /* Incidence of H as CSR + CSC (Section III: the hyperedge/vertex incidence
  * and its bipartite form).  All pointers are device pointers. */
@@ -377,19 +377,20 @@ int slg_count_noalloc(const slg_hypergraph *h, int32_t s, uint32_t flags,
                       int64_t *n_pairs, void *stream);
 
 /* Statistics of the last call made by this host thread.  Bins: 0 = warp
- * (small rows), 1 = CTA small, 2 = CTA large, 3 = giant rows. */
+ * (small rows), 1 = CTA small, 2 = CTA large, 3 = giant rows (dense in their
+ * id span, s = 1, or dense-core rows), 4 = sparse large rows (s >= 2). */
 typedef struct slg_stats {
   int64_t wedges;          /* W_s visited */
   int64_t pairs;           /* |L_s| */
   int64_t rows_active;     /* rows with size >= s */
-  int64_t rows_bin[4];     /* rows per bin */
-  int64_t wedges_bin[4];   /* wedges per bin */
-  int64_t incid_bin[4];    /* CSR incidences of the rows of each bin */
-  int64_t pairs_bin[4];    /* pairs emitted by each bin */
+  int64_t rows_bin[5];     /* rows per bin */
+  int64_t wedges_bin[5];   /* wedges per bin */
+  int64_t incid_bin[5];    /* CSR incidences of the rows of each bin */
+  int64_t pairs_bin[5];    /* pairs emitted by each bin */
   int32_t kernel_launches; /* kernels launched by the call */
   int32_t profiled;        /* 1 if the ms_* fields below were measured */
   float ms_plan;           /* validation, maps, filtered CSC, bins */
-  float ms_walk[4];        /* the walk kernel of each bin */
+  float ms_walk[5];        /* the walk kernel of each bin */
   float ms_scan;           /* row offsets */
   float ms_gather;         /* output assembly */
   int64_t core_rows;       /* dense core used by SLG_TENSOR_CORE: rows, */

@@ -72,14 +72,14 @@ class _Hypergraph(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [("wedges", ctypes.c_int64), ("pairs", ctypes.c_int64),
                 ("rows_active", ctypes.c_int64),
-                ("rows_bin", ctypes.c_int64 * 4),
-                ("wedges_bin", ctypes.c_int64 * 4),
-                ("incid_bin", ctypes.c_int64 * 4),
-                ("pairs_bin", ctypes.c_int64 * 4),
+                ("rows_bin", ctypes.c_int64 * 5),
+                ("wedges_bin", ctypes.c_int64 * 5),
+                ("incid_bin", ctypes.c_int64 * 5),
+                ("pairs_bin", ctypes.c_int64 * 5),
                 ("kernel_launches", ctypes.c_int32),
                 ("profiled", ctypes.c_int32),
                 ("ms_plan", ctypes.c_float),
-                ("ms_walk", ctypes.c_float * 4),
+                ("ms_walk", ctypes.c_float * 5),
                 ("ms_scan", ctypes.c_float),
                 ("ms_gather", ctypes.c_float),
                 ("core_rows", ctypes.c_int64),

@@ -301,6 +301,18 @@ cudaError_t giant_scratch(Call &c, int32_t max_work, WalkLaunch *L) {
   return e;
 }
 
+// Per-CTA scratch of the sparse bin (staged builds only): the pairs of one
+// row, at most half its wedges, as j then w.
+cudaError_t sparse_scratch(Call &c, int32_t max_work, WalkLaunch *L) {
+  L->sparse_scratch = nullptr;
+  L->sparse_stride = 0;
+  if (max_work <= 0 || L->a.mode != kStage) return cudaSuccess;
+  const long long stride = 2ll * (max_work / 2 + 1);
+  cudaError_t e = c.pool->get(&L->sparse_scratch, (size_t)sparse_ctas() * (size_t)stride);
+  if (e == cudaSuccess) L->sparse_stride = stride;
+  return e;
+}
+
 thread_local int32_t t_err_where = 0;  // kWhere* of the last device-raised error
 
 int read_meta(Call &c) {
@@ -458,9 +470,12 @@ int run_binned(Call &c, int64_t *result) {
                                 ? std::max(c.meta_host->max_giant_work, (int32_t)1) +
                                       (core.T ? core.n_core : 0)
                                 : 0;
+  const int32_t max_sparse =
+      c.meta_host->rows_bin[kBinSparse] ? std::max(c.meta_host->max_sparse_work, (int32_t)1) : 0;
   WalkLaunch L = walk_launch(c, c.op == kOpBuild ? kStage : kCount, c.smin, c.row_begin);
   L.a.core = core;
   SLG_TRY(giant_scratch(c, max_giant, &L));
+  SLG_TRY(sparse_scratch(c, max_sparse, &L));
   L.w.r_off = c.sd.r_off;
   L.w.r_idx = c.sd.r_idx;
   L.w.c_idx_s = w.c_idx_s;
@@ -491,6 +506,7 @@ int run_binned(Call &c, int64_t *result) {
     } else {
       // Staging too small: walk again, writing straight to the output.
       SLG_TRY(cudaMemsetAsync(&w.meta->giant_ticket, 0, sizeof(unsigned int), c.st));
+      SLG_TRY(cudaMemsetAsync(&w.meta->sparse_ticket, 0, sizeof(unsigned int), c.st));
       L.a.mode = kDirect;
       L.a.row_ptr = w.row_ptr;
       L.a.out_i = c.out_i;
@@ -844,6 +860,8 @@ struct slg_plan {
   slg::Work w = {};
   int32_t *giant = nullptr;
   long long giant_stride = 0;
+  int32_t *sparse = nullptr;
+  long long sparse_stride = 0;
   int32_t *out_i = nullptr, *out_j = nullptr, *out_w = nullptr;
   long long *offsets = nullptr;    // [count + 1]
   int64_t pairs = 0;
@@ -897,6 +915,8 @@ cudaError_t enqueue_plan(slg_plan *p, const Bins &bins, cudaStream_t st, int32_t
   L.R = sd.R;
   L.giant_scratch = p->giant;
   L.giant_stride = p->giant_stride;
+  L.sparse_scratch = p->sparse;
+  L.sparse_stride = p->sparse_stride;
   int32_t n = 0;
   if (sd.R > 0) PLAN_TRY(launch_walk(L, st, &n));
   PLAN_TRY(launch_row_scan(sd.R, w, st));
@@ -1343,6 +1363,8 @@ extern "C" int slg_plan_create(const slg_hypergraph *hs, const int32_t *s, int32
   if (max_work > 0) {
     p->giant_stride = 4ll * max_work;
     SLG_TRY(p->mem.get(&p->giant, (size_t)giant_ctas() * (size_t)p->giant_stride));
+    p->sparse_stride = 2ll * (max_work / 2 + 1);
+    SLG_TRY(p->mem.get(&p->sparse, (size_t)sparse_ctas() * (size_t)p->sparse_stride));
   }
   // 4. autotuner: bin thresholds, timed on this batch
   const Bins cands[] = {Bins{}, Bins{64, 1024, 4096}, Bins{128, 512, 4096}, Bins{128, 1024, 2048},

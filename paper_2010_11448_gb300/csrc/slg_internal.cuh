@@ -19,8 +19,13 @@ namespace slg {
 constexpr int kWarp = 32;
 constexpr int32_t kEmpty = -1;
 
-// Row bins by wedge work (the degree-binned scheduler).
-enum Bin : int { kBinWarp = 0, kBinCtaS = 1, kBinCtaL = 2, kBinGiant = 3, kNumBins = 4 };
+// Row bins by wedge work (the degree-binned scheduler).  Rows above the CTA
+// bins go to the sparse bin when their far ends are sparse in their id span
+// (fewer than one wedge per kDenseRatio ids) and their threshold is at least
+// 2, else to the giant bin (dense rows, s = 1, dense-core rows).
+enum Bin : int {
+  kBinWarp = 0, kBinCtaS = 1, kBinCtaL = 2, kBinGiant = 3, kBinSparse = 4, kNumBins = 5
+};
 
 // Upper bounds on a row's wedge count for each non-giant bin.  The hash tables
 // hold twice the bound, so a row can never fill its table (distinct
@@ -34,6 +39,12 @@ constexpr int32_t kCtaLMaxWork = 4096;
 #define SLG_GIANT_HUGE_WORK 32768
 #endif
 constexpr int32_t kGiantHugeWork = SLG_GIANT_HUGE_WORK;
+// A row is dense when it has at least one wedge per this many ids of its far
+// ends' span (swept: 8 best for the giant bin's dense windows).
+#ifndef SLG_DENSE_RATIO
+#define SLG_DENSE_RATIO 8
+#endif
+constexpr int kDenseRatio = SLG_DENSE_RATIO;
 
 // Counters the device writes and the host reads once per call.
 struct Meta {
@@ -51,6 +62,10 @@ struct Meta {
   unsigned int giant_ticket;           // dynamic giant-row scheduling
   unsigned int giant_huge;             // giant rows above kGiantHugeWork (front of the list)
   unsigned int giant_rest;             // the other giant rows (back of the list)
+  unsigned int sparse_ticket;          // the same three for the sparse bin
+  unsigned int sparse_huge;
+  unsigned int sparse_rest;
+  int32_t max_sparse_work;             // largest work of a sparse-bin row
   int32_t kept;                        // entries of the filtered CSC
   int32_t max_giant_work;              // largest work of a giant-bin row
   unsigned long long nnz_core;         // incidences of the dense core
@@ -238,8 +253,15 @@ __device__ __forceinline__ int32_t s_of(const int32_t *row_s, int32_t smin, int3
 
 // Wedge-work thresholds of the bins (runtime; each at most the capacity the
 // bin's kernel is compiled for: kWarpMaxWork, kCtaSMaxWork, kCtaLMaxWork).
+// `sparse`: sparse rows above the CTA bins up to this work take the sparse
+// bin (larger ones hold more repeated far ends per window than its table,
+// and the giant bin's partition serves them better); 0 turns the bin off.
+#ifndef SLG_SPARSE_MAX_WORK
+#define SLG_SPARSE_MAX_WORK 16384
+#endif
 struct Bins {
   int32_t warp = kWarpMaxWork, ctas = kCtaSMaxWork, ctal = kCtaLMaxWork;
+  int32_t sparse = SLG_SPARSE_MAX_WORK;
 };
 
 // Dense core for the tensor-core tile path (all null / 0 when unused).
@@ -339,11 +361,15 @@ struct WalkLaunch {
   int32_t rows;             // rows in the range (list stride)
   int32_t *giant_scratch;   // [giant_ctas][4 * max giant work] wedge ends + pairs
   long long giant_stride;   // ints per giant CTA
+  int32_t *sparse_scratch;  // [sparse_ctas][stride] staged pairs (j, w) of a sparse row
+  long long sparse_stride;  // ints per sparse CTA (>= the row's work: pairs <= work / 2)
   int32_t R;                // rows of the side (far ends lie in [0, R))
 };
 
-// CTAs of the giant kernel (one per SM) and the largest side it supports.
+// CTAs of the giant kernel (two per SM), of the sparse kernel (one per SM),
+// and the largest side they support.
 int giant_ctas();
+int sparse_ctas();
 constexpr int32_t kGiantMaxR = 1 << 24;
 
 // ev (optional): kNumBins + 1 events recorded before the first and after

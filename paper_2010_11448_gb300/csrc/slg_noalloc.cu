@@ -19,7 +19,7 @@ namespace {
 // 64 MiB of int32, zero at load; every GPU that loads the library keeps it
 // until the process exits.
 constexpr long long kNoallocInts = 16ll * 1024 * 1024;
-constexpr int kNoallocResultInts = 64;  // Meta (error word, totals), 256 B aligned
+constexpr int kNoallocResultInts = 128;  // Meta (error word, totals), 512 B, aligned
 constexpr int kNoallocNT = 256;
 constexpr int kNoallocMaxWarps = 1024;
 

@@ -192,7 +192,7 @@ __global__ __launch_bounds__(kRowsNT) void k_rows_work(Side s, int32_t smin, int
   if (meta->err) return;
   __shared__ int32_t s_work[kRowsPerBlock];
   __shared__ int32_t s_cnt[kNumBins], s_base[kNumBins];
-  __shared__ int32_t s_hcnt, s_hbase;  // giant rows above kGiantHugeWork
+  __shared__ int32_t s_hcnt[2], s_hbase[2];  // giant / sparse rows above kGiantHugeWork
   __shared__ unsigned long long s_w[kNumBins], s_k[kNumBins];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int32_t r0 = row_begin + blockIdx.x * kRowsPerBlock;
@@ -201,7 +201,7 @@ __global__ __launch_bounds__(kRowsNT) void k_rows_work(Side s, int32_t smin, int
     s_w[threadIdx.x] = 0;
     s_k[threadIdx.x] = 0;
   }
-  if (threadIdx.x == 0) s_hcnt = 0;
+  if (threadIdx.x < 2) s_hcnt[threadIdx.x] = 0;
   for (int i = warp; i < kRowsPerBlock; i += kRowsNT / 32) {
     const int32_t e = r0 + i;
     int32_t work = 0;
@@ -259,28 +259,39 @@ __global__ __launch_bounds__(kRowsNT) void k_rows_work(Side s, int32_t smin, int
     const bool forced = my_work < 0;
     if (forced) my_work = -1 - my_work;
     if (my_work > 0 || forced) {
-      my_bin = forced ? (int)kBinGiant : bin_of(my_work, bins);
-      if (my_bin == kBinGiant) atomicMax(&meta->max_giant_work, my_work);
-      huge = my_bin == kBinGiant && my_work > kGiantHugeWork;
-      my_slot = huge ? atomicAdd(&s_hcnt, 1) : atomicAdd(&s_cnt[my_bin], 1);
-      atomicAdd(&s_w[my_bin], (unsigned long long)my_work);
       const int32_t e = r0 + threadIdx.x;
+      my_bin = forced ? (int)kBinGiant : bin_of(my_work, bins);
+      // a large row up to bins.sparse wedges whose far ends are sparse in
+      // its span (f in (e, R)) and whose threshold is at least 2 takes the
+      // sparse bin
+      if (my_bin == kBinGiant && !forced && my_work <= bins.sparse &&
+          s_of(s.row_s, smin, e) >= 2 &&
+          (long long)my_work * kDenseRatio < (long long)(s.R - 1 - e))
+        my_bin = kBinSparse;
+      if (my_bin == kBinGiant) atomicMax(&meta->max_giant_work, my_work);
+      if (my_bin == kBinSparse) atomicMax(&meta->max_sparse_work, my_work);
+      huge = (my_bin == kBinGiant || my_bin == kBinSparse) && my_work > kGiantHugeWork;
+      my_slot = huge ? atomicAdd(&s_hcnt[my_bin == kBinSparse], 1) : atomicAdd(&s_cnt[my_bin], 1);
+      atomicAdd(&s_w[my_bin], (unsigned long long)my_work);
       atomicAdd(&s_k[my_bin], (unsigned long long)(s.r_off[e + 1] - s.r_off[e]));
     }
   }
   __syncthreads();
   if (threadIdx.x < kNumBins) {
     const int b = threadIdx.x;
-    if (b != kBinGiant) {
+    if (b != kBinGiant && b != kBinSparse) {
       s_base[b] = s_cnt[b] ? (int32_t)atomicAdd(&meta->rows_bin[b], (unsigned long long)s_cnt[b]) : 0;
     } else {
-      // the giant bin's huge rows fill its list from the front, the others
-      // from the back (k_walk_giant hands out the huge ones first); rows_bin
-      // counts both
-      if (s_cnt[b] + s_hcnt)
-        atomicAdd(&meta->rows_bin[b], (unsigned long long)(s_cnt[b] + s_hcnt));
-      s_base[b] = s_cnt[b] ? (int32_t)atomicAdd(&meta->giant_rest, (unsigned)s_cnt[b]) : 0;
-      s_hbase = s_hcnt ? (int32_t)atomicAdd(&meta->giant_huge, (unsigned)s_hcnt) : 0;
+      // the huge rows of the giant and sparse bins fill their list from the
+      // front, the others from the back (the kernels hand out the huge ones
+      // first); rows_bin counts both
+      const int q = b == kBinSparse;
+      unsigned *rest = q ? &meta->sparse_rest : &meta->giant_rest;
+      unsigned *hge = q ? &meta->sparse_huge : &meta->giant_huge;
+      if (s_cnt[b] + s_hcnt[q])
+        atomicAdd(&meta->rows_bin[b], (unsigned long long)(s_cnt[b] + s_hcnt[q]));
+      s_base[b] = s_cnt[b] ? (int32_t)atomicAdd(rest, (unsigned)s_cnt[b]) : 0;
+      s_hbase[q] = s_hcnt[q] ? (int32_t)atomicAdd(hge, (unsigned)s_hcnt[q]) : 0;
     }
     if (s_w[b]) {
       atomicAdd(&meta->wedges_bin[b], s_w[b]);
@@ -300,8 +311,8 @@ __global__ __launch_bounds__(kRowsNT) void k_rows_work(Side s, int32_t smin, int
   if (my_bin >= 0) {
     const int64_t len = row_end - row_begin;
     int64_t pos = s_base[my_bin] + my_slot;
-    if (huge) pos = s_hbase + my_slot;
-    else if (my_bin == kBinGiant) pos = len - 1 - pos;
+    if (huge) pos = s_hbase[my_bin == kBinSparse] + my_slot;
+    else if (my_bin == kBinGiant || my_bin == kBinSparse) pos = len - 1 - pos;
     bin_rows[(int64_t)my_bin * len + pos] = r0 + threadIdx.x;
   }
 }

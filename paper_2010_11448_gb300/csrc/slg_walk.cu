@@ -561,9 +561,6 @@ __global__ __launch_bounds__(NT, MINB) void k_walk_cta(Walk w, const int32_t *__
 #ifndef SLG_GIANT_MINB
 #define SLG_GIANT_MINB 2
 #endif
-#ifndef SLG_DENSE_RATIO
-#define SLG_DENSE_RATIO 8  // a row is dense with >= 1 wedge per this many ids (swept: 8 best)
-#endif
 constexpr int kGiantNT = SLG_GIANT_NT;
 constexpr int kGiantTMax = SLG_GIANT_TMAX;
 constexpr int kNSBLog = 11;
@@ -693,7 +690,7 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
     const int32_t work = a.row_work[e - a.row_begin];
     // Dense rows (at least one wedge per 8 ids) count fixed windows of
     // kDenseW ids in a dense shared array: no hashing, no sort.
-    const bool dense = (long long)work * SLG_DENSE_RATIO >= (long long)span;
+    const bool dense = (long long)work * kDenseRatio >= (long long)span;
     if (work > q4) {  // the scratch is sized by the largest row: cannot happen
       if (threadIdx.x == 0) raise_error(meta, SLG_ERR_INVALID, kWhereGiant);
       break;
@@ -971,6 +968,236 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
   }
 }
 
+// ------------------------------------------------------------ sparse bin --
+//
+// Large rows whose far ends are sparse in their id span, with s >= 2.  Almost
+// every far end of such a row occurs once (on the Chung-Lu workloads about
+// 96 % of the wedges of these rows are the only wedge to their far end), and
+// a far end with a single wedge can never reach s >= 2.  So a CTA (one per
+// SM) keeps one bit per id of a window of the span: the first wedge to f sets
+// f's bit (one shared atomicOr) and does nothing else; only a wedge that finds
+// the bit already set -- a repeat -- goes to a small shared hash table, whose
+// count word holds the repeats of f minus one.  |e ∩ f| = repeats + 1, and f
+// is listed as a survivor when that reaches s, as in the other bins.
+//
+// Window: 2^kSpWinLog ids of the span [f_lo, R), processed in ascending
+// order, so the row's output comes out sorted.  If a window's distinct
+// repeated far ends exceed what the table holds (kSpClaims), the window is
+// given up -- its bits and table cleared -- and redone at half the width (a
+// window of at most kSpClaims ids can never overflow).  The first walk of a
+// row of at most kSpCache wedges keeps every far end in shared memory; its
+// later windows read them from there instead of walking again, and its bits
+// are cleared from them instead of over the whole window.
+
+constexpr int kSpNT = 1024;
+constexpr int kSpWinLog = 20;                    // ids per window (bitmap 128 KB)
+constexpr int kSpWords = 1 << (kSpWinLog - 5);
+constexpr int kSpCache = 8192;                   // far ends kept of a small row
+constexpr int kSpT = 4096;                       // repeats table slots (32 KB)
+constexpr int kSpLgT = 12;
+constexpr int kSpClaims = kSpT / 2;              // distinct repeated far ends per window
+constexpr int kSpList = kSpClaims;               // survivors per window (<= claims)
+constexpr int kSpQ = kSpList / kSpNT;
+constexpr int kSpG = 6;                          // wedges per thread per walk step
+static_assert(kSpT == 1 << kSpLgT && kSpQ * kSpNT >= kSpList, "sparse bin geometry");
+
+// [s_base 8][s_flag 8: overflow, claims][s_row 4][pad 12][bitmap kSpWords x 4]
+// [table kSpT x 8][cache kSpCache x 4][s_beg NT][s_pref NT+1][ws NT/32+1]
+// [list kSpList][list count 1]
+constexpr size_t sparse_smem() {
+  return 32 + (size_t)kSpWords * 4 + (size_t)kSpT * 8 + (size_t)kSpCache * 4 +
+         (size_t)(2 * kSpNT + 1 + kSpNT / 32 + 1) * 4 + (size_t)(kSpList + 1) * 4;
+}
+
+// A repeat of far end f (its bit was already set).  The first repeat claims
+// f's slot (32-bit CAS on the key word; the count word stays 0 = one
+// repeat), later ones add to the count word.  Unweighted: a pair that reached
+// s is not counted further.  Once the window has overflowed nothing is
+// inserted (the window will be redone).
+__device__ __forceinline__ void sparse_repeat(unsigned long long *tab, int32_t f, int32_t smin,
+                                              bool unweighted, int32_t *s_flag,
+                                              const SurvList &sl) {
+  if (*(volatile int32_t *)s_flag) return;
+  uint32_t h = ((uint32_t)f * 0x9E3779B1u) >> (32 - kSpLgT);
+  for (int probe = 0; probe < kSpT; ++probe) {
+    uint32_t *cw = count_word(tab, h);
+    const uint32_t k = atomicCAS(cw + 1, 0xFFFFFFFFu, (uint32_t)f);
+    if (k == 0xFFFFFFFFu) {  // first repeat: |e ∩ f| = 2 so far
+      if (atomicAdd(s_flag + 1, 1) >= kSpClaims) {
+        *(volatile int32_t *)s_flag = 1;  // too many: the window is redone narrower
+        return;
+      }
+      if (smin <= 2) {
+        const int32_t p = atomicAdd(sl.n, 1);
+        if (p < sl.cap) sl.slot[p] = (int32_t)h;
+      }
+      return;
+    }
+    if (k == (uint32_t)f) {  // count word = repeats - 1, |e ∩ f| = count word + 2
+      if (unweighted && (int32_t)*(volatile uint32_t *)cw + 2 >= smin) return;
+      const int32_t old = (int32_t)atomicAdd(cw, 1u);
+      if (old + 2 < smin && old + 3 >= smin) {
+        const int32_t p = atomicAdd(sl.n, 1);
+        if (p < sl.cap) sl.slot[p] = (int32_t)h;
+      }
+      return;
+    }
+    h = (h + 1) & (kSpT - 1);
+  }
+  // unreachable: claims stop at kSpClaims + kSpNT < kSpT, so a free slot exists
+  *(volatile int32_t *)s_flag = 1;
+}
+
+__global__ __launch_bounds__(kSpNT, 1) void k_walk_sparse(Walk w, const int32_t *__restrict__ rows,
+                                                          EmitArgs a, int32_t *__restrict__ scratch,
+                                                          long long scratch_stride, int32_t R,
+                                                          int32_t list_len) {
+  Meta *meta = a.meta;
+  if (meta->err) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  long long *s_base = reinterpret_cast<long long *>(smem);
+  int32_t *s_flag = reinterpret_cast<int32_t *>(smem + 8);  // [0] overflow, [1] claims
+  int32_t *s_row = reinterpret_cast<int32_t *>(smem + 16);
+  uint32_t *bm = reinterpret_cast<uint32_t *>(smem + 32);
+  unsigned long long *tab = reinterpret_cast<unsigned long long *>(bm + kSpWords);
+  int32_t *cache = reinterpret_cast<int32_t *>(tab + kSpT);
+  int32_t *s_beg = cache + kSpCache;
+  int32_t *s_pref = s_beg + kSpNT;
+  int32_t *ws = s_pref + kSpNT + 1;
+  const SurvList sl = {ws + kSpNT / 32 + 1, ws + kSpNT / 32 + 1 + kSpList, kSpList};
+  // per-CTA global scratch: the row's staged pairs, j then w (<= work / 2 each)
+  const long long half = scratch_stride / 2;
+  int32_t *tj = scratch ? scratch + (long long)blockIdx.x * scratch_stride : nullptr;
+  int32_t *tw = tj ? tj + half : nullptr;
+
+  {
+    uint4 *b4 = reinterpret_cast<uint4 *>(bm);
+    for (int i = threadIdx.x; i < kSpWords / 4; i += kSpNT) b4[i] = make_uint4(0, 0, 0, 0);
+  }
+  for (int i = threadIdx.x; i < kSpT; i += kSpNT) tab[i] = kEmpty64;
+  if (threadIdx.x == 0) {
+    *sl.n = 0;
+    s_flag[0] = 0;
+    s_flag[1] = 0;
+  }
+  const unsigned nrows = (unsigned)meta->rows_bin[kBinSparse];
+  const unsigned nhuge = meta->sparse_huge;
+  const bool unweighted = a.unweighted != 0;
+  const bool emit = a.mode != kCount;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned t = atomicAdd(&meta->sparse_ticket, 1u);
+      s_flag[0] = 0;  // overflow
+      s_flag[1] = 0;  // claims of the window
+      *s_row = t >= nrows ? -1 : rows[t < nhuge ? t : list_len - 1 - (t - nhuge)];
+    }
+    __syncthreads();
+    const int32_t e = *s_row;
+    if (e < 0) break;
+    const int32_t smin = s_of(a.row_s, a.smin, e);
+    const int32_t f_lo = a.full_rows ? 0 : e + 1;
+    const int32_t work = a.row_work[e - a.row_begin];
+    const bool cached = work <= kSpCache;
+    if (a.mode == kStage && (long long)work / 2 > half) {  // scratch sized by the largest row
+      if (threadIdx.x == 0) raise_error(meta, SLG_ERR_INVALID, kWhereGiant);
+      break;
+    }
+    long long base = -1;
+    if (a.mode == kDirect) base = a.row_ptr[e - a.row_begin];
+    int32_t out = 0;  // pairs of the row so far
+    int32_t width = 1 << kSpWinLog;
+    bool first = true;
+    for (int32_t wlo = f_lo; wlo < R;) {
+      const int32_t whi = (R - wlo > width) ? wlo + width : R;
+      auto visit = [&](int32_t f) {
+        if (f >= wlo && f < whi) {
+          const uint32_t b = (uint32_t)(f - wlo), m = 1u << (b & 31);
+          if (atomicOr(bm + (b >> 5), m) & m)
+            sparse_repeat(tab, f, smin, unweighted, s_flag, sl);
+        }
+      };
+      __syncthreads();  // flags reset, bits and table clear
+      if (first || !cached) {
+        const bool keep = first && cached;
+        cta_walk<kSpNT, kSpG>(w, w.r_off[e], w.r_off[e + 1], s_beg, s_pref, ws,
+                              [&](int32_t f, int32_t i) {
+                                if (keep) cache[i] = f;
+                                visit(f);
+                              });
+      } else {
+        for (int32_t i = threadIdx.x; i < work; i += kSpNT) visit(cache[i]);
+      }
+      first = false;
+      __syncthreads();  // every insert done
+      const bool overflow = s_flag[0] != 0;
+      int32_t n = 0, at = 0, used = 0;
+      if (!overflow)  // survivors, table cleared, sorted at tab[at, at + n)
+        n = table_collect_list<kSpNT, kSpQ>(tab, kSpT, sl, emit, &at, &used);
+      // bits of the window back to zero
+      if (cached) {
+        __syncthreads();
+        for (int32_t i = threadIdx.x; i < work; i += kSpNT) {
+          const int32_t f = cache[i];
+          if (f >= wlo && f < whi) bm[(uint32_t)(f - wlo) >> 5] = 0u;
+        }
+      } else {
+        uint4 *b4 = reinterpret_cast<uint4 *>(bm);
+        const int32_t nw4 = (int32_t)((((uint32_t)(whi - wlo) + 31u) >> 5) + 3) >> 2;
+        for (int32_t i = threadIdx.x; i < nw4; i += kSpNT) b4[i] = make_uint4(0, 0, 0, 0);
+      }
+      if (overflow) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < kSpT; i += kSpNT) tab[i] = kEmpty64;
+        if (threadIdx.x == 0) {
+          *sl.n = 0;
+          s_flag[0] = 0;
+          s_flag[1] = 0;
+        }
+        if (width <= kSpClaims) {  // cannot overflow: a bound was broken
+          if (threadIdx.x == 0) raise_error(meta, SLG_ERR_INVALID, kWhereHash);
+          break;
+        }
+        width >>= 1;  // retry the same ids, narrower (uniform decision)
+        continue;
+      }
+      if (a.mode == kStage && out + n > half) {
+        if (threadIdx.x == 0) raise_error(meta, SLG_ERR_INVALID, kWhereGiant);
+        table_reset_front<kSpNT>(tab, used);
+        break;
+      }
+      if (emit && n > 0) {
+        for (int32_t i = threadIdx.x; i < n; i += kSpNT) {
+          const unsigned long long x = tab[at + i];
+          // table_collect_list added one to the count word: repeats; + 1
+          const int32_t f = (int32_t)(x >> 32), c = (int32_t)(uint32_t)x + 1;
+          if (a.mode == kDirect) {
+            put(a, base, out + i, e, f, c);
+          } else {
+            tj[out + i] = f;
+            if (!unweighted) tw[out + i] = c;
+          }
+        }
+      }
+      out += n;
+      table_reset_front<kSpNT>(tab, used);
+      if (threadIdx.x == 0) s_flag[1] = 0;
+      wlo = whi;
+      if (width < (1 << kSpWinLog)) width <<= 1;
+    }
+    if (threadIdx.x == 0) *s_base = reserve(a, e, out, kBinSparse);
+    __syncthreads();
+    if (a.mode == kStage) {
+      const long long b = *s_base;
+      if (b >= 0)
+        for (int32_t i = threadIdx.x; i < out; i += kSpNT) {
+          a.stage_j[b + i] = tj[i];
+          if (!unweighted) a.stage_w[b + i] = tw[i];
+        }
+    }
+  }
+}
+
 // --------------------------------------------------------------- launch --
 
 namespace {
@@ -981,7 +1208,7 @@ using CfgL = CtaCfg<256, 2 * kCtaLMaxWork>;
 #define K_CTA_L k_walk_cta<256, 2 * kCtaLMaxWork, kBinCtaL, 3>
 
 struct Occ {
-  int sms = 0, warp_blocks = 0, s_blocks = 0, l_blocks = 0, g_blocks = 0;
+  int sms = 0, warp_blocks = 0, s_blocks = 0, l_blocks = 0, g_blocks = 0, sp_blocks = 0;
   int dev = -1;
 };
 
@@ -1004,6 +1231,11 @@ Occ &occ_for_device() {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.g_blocks, k_walk_giant, kGiantNT,
                                                   giant_smem());
     if (o.g_blocks < 1) o.g_blocks = 1;
+    cudaFuncSetAttribute(k_walk_sparse, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sparse_smem());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.sp_blocks, k_walk_sparse, kSpNT,
+                                                  sparse_smem());
+    if (o.sp_blocks < 1) o.sp_blocks = 1;
     o.dev = dev;
   }
   return o;
@@ -1017,6 +1249,11 @@ int giant_ctas_for_device() {
 }
 
 int giant_ctas() { return giant_ctas_for_device(); }
+
+int sparse_ctas() {
+  Occ &o = occ_for_device();
+  return o.sms * o.sp_blocks;
+}
 
 cudaError_t launch_walk(const WalkLaunch &L, cudaStream_t st, int32_t *launches,
                         cudaEvent_t *ev) {
@@ -1043,6 +1280,10 @@ cudaError_t launch_walk(const WalkLaunch &L, cudaStream_t st, int32_t *launches,
     ++n;
   }
   if (ev) cudaEventRecord(ev[4], st);
+  k_walk_sparse<<<o.sms * o.sp_blocks, kSpNT, sparse_smem(), st>>>(
+      L.w, lists + 4 * stride, L.a, L.sparse_scratch, L.sparse_stride, L.R, (int32_t)stride);
+  ++n;
+  if (ev) cudaEventRecord(ev[5], st);
   if (launches) *launches += n;
   return cudaGetLastError();
 }

@@ -69,15 +69,17 @@ def test_unweighted_batch_pairs():
 
 
 def test_union_beyond_one_super_chunk():
-    # two members with giant rows first, then a filler of 4.2M small rows:
+    # two members with large rows first, then a filler of 4.2M small rows:
     # the union has more than 4M rows, so the early rows' id span covers
-    # several super-chunks of the giant bin while all their far ends lie in
-    # the first one (the later super-chunks are empty for them)
+    # several super-chunks of the giant bin (member 0, s = 1: its large rows
+    # take the giant bin) or several windows of the sparse bin (member 1,
+    # s = 3) while all their far ends lie in the first one (the later ones
+    # are empty for them)
     gs = [hg.chung_lu(20_000, 40_000, seed=61, size_cap=4000),
           hg.lognormal_web(20_000, 40_000, seed=62, cap=2000, core_edges=256,
                            core_vertices=512, core_density=0.3),
           hg.uniform(4_200_000, 600_000, 1, 3, seed=3)]
-    ss = [2, 3, 2]
+    ss = [1, 3, 2]
     dhs = [slg.to_device(h) for h in gs]
     plan = slg.Plan(dhs, ss)
     for _ in range(3):

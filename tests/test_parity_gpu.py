@@ -110,6 +110,8 @@ def test_medium_all_bins(medium, dual, s):
     assert st["wedges"] == oracle.wedges(m, n, off, idx, s)
     if s <= 4:
         assert st["rows_bin"][3] > 0, "giant bin not exercised"
+    if dual and s >= 2:
+        assert st["rows_bin"][4] > 0, "sparse bin not exercised"
 
 
 def test_medium_unweighted_same_pairs(medium):
@@ -311,8 +313,8 @@ def test_chung_lu_1m_sampled_rows(chung_lu_1m, dual, s):
 
 def test_ids_beyond_one_super_chunk():
     # the dual of 1500 large hyperedges over 5M vertices: rows are vertices,
-    # far-end ids span up to 5M, beyond the 4M ids one super-chunk of the
-    # giant bin covers, so giant rows cross several super-chunks
+    # far-end ids span up to 5M.  At s >= 2 the large rows are sparse in that
+    # span and cross several windows of the sparse bin.
     h = hg.uniform(1500, 5_000_000, 500, 6000, seed=9)
     dh = slg.to_device(h)
     m, n, off, idx = oracle.side(h, True)
@@ -322,8 +324,31 @@ def test_ids_beyond_one_super_chunk():
     for s in (2, 3):
         got = gpu_lg(dh, s, dual=True)
         st = slg.last_stats()
-        assert st["rows_bin"][3] > 0  # giant rows present
+        assert st["rows_bin"][4] > 0  # sparse large rows present
         sel = got[np.isin(got[:, 0], rows)]
         want = oracle.canonical(*oracle.line_graph(m, n, off, idx, s, rows=rows, threads=16))
         assert np.array_equal(sel, want), s
         assert got.shape[0] == slg.count(dh, s, dual=True)
+
+
+def test_giant_rows_beyond_one_super_chunk():
+    # s = 1 sends every large row to the giant bin.  The dual of one
+    # hyperedge of 8000 random vertices out of 5M (plus small hyperedges):
+    # its first ~1800 vertices have more than 6144 wedges (the giant bin's
+    # partitioned rows), and their far-end span (v, 5M) covers more than the
+    # 4M ids of one super-chunk of the giant bin, most of them empty.
+    rng = np.random.default_rng(12)
+    n = 5_000_000
+    big = np.sort(rng.choice(n, 8000, replace=False))
+    small = [np.sort(rng.choice(n, int(k), replace=False)) for k in rng.integers(2, 40, 3000)]
+    h = hg.from_rows([big] + small, n)
+    dh = slg.to_device(h)
+    m, n_, off, idx = oracle.side(h, True)
+    rows = np.unique(np.concatenate([big[:2000:3], np.arange(0, m, 4999)])).astype(np.int32)
+    got = gpu_lg(dh, 1, dual=True)
+    st = slg.last_stats()
+    assert st["rows_bin"][3] > 0 and st["rows_bin"][4] == 0
+    sel = got[np.isin(got[:, 0], rows)]
+    want = oracle.canonical(*oracle.line_graph(m, n_, off, idx, 1, rows=rows, threads=16))
+    assert np.array_equal(sel, want)
+    assert got.shape[0] == slg.count(dh, 1, dual=True)
