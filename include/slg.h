@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define SLG_ABI_VERSION 2
+#define SLG_ABI_VERSION 3
 
 /* Incidence of H as CSR + CSC (Section III: the hyperedge/vertex incidence
  * and its bipartite form).  All pointers are device pointers. */
@@ -185,6 +185,65 @@ int slg_row_offsets(const slg_hypergraph *h, int32_t s, uint32_t flags,
 int slg_build_host(const slg_hypergraph *h, int32_t s, uint32_t flags,
                    int32_t *out_i, int32_t *out_j, int32_t *out_w,
                    int64_t capacity, int64_t *n_pairs, void *stream);
+
+/*
+ * slg_build_csr -- slg_build's edge list in compressed row form: the pairs
+ * of row i (the pairs (i, j) with i < j, ascending j) are
+ * out_j[row_ptr[i] .. row_ptr[i + 1]) with their weights in out_w, so the
+ * i of each pair is implied and not written.  This is L_s (Section III) as
+ * the adjacency of its upper triangle; it moves a third fewer bytes than
+ * the (i, j, w) triples.
+ *   row_ptr  DEVICE int64 array of R + 1 entries (R = rows of the side);
+ *            row_ptr[R] = |L_s|
+ *   out_j, out_w, capacity, n_pairs  as for slg_build
+ *   flags    as for slg_build except SLG_ALGO_SPGEMM and the relabel flags
+ *            (SLG_ERR_UNSUPPORTED)
+ * Synchronises `stream`.  Errors as for slg_build.
+ */
+int slg_build_csr(const slg_hypergraph *h, int32_t s, uint32_t flags,
+                  int64_t *row_ptr, int32_t *out_j, int32_t *out_w,
+                  int64_t capacity, int64_t *n_pairs, void *stream);
+
+/*
+ * One query of slg_build_host_many: L_s of the hypergraph or of its dual.
+ *   s, flags   as for slg_build (SLG_ASYNC is not accepted)
+ *   row_ptr    HOST int64 array of R + 1 entries for the compressed row form
+ *              of slg_build_csr (out_i unused, may be NULL), or NULL for the
+ *              (i, j, w) triples of slg_build
+ *   out_i, out_j, out_w, capacity   HOST arrays as for slg_build_host
+ *   n_pairs    out: |L_s| (also when it exceeds capacity)
+ *   status     out: this query's slg_status
+ */
+typedef struct slg_query {
+  int32_t s;
+  uint32_t flags;
+  int64_t *row_ptr;
+  int32_t *out_i, *out_j, *out_w;
+  int64_t capacity;
+  int64_t n_pairs;
+  int32_t status;
+} slg_query;
+
+/*
+ * slg_build_host_many -- several line graphs of one hypergraph given in
+ * HOST memory (h holds host pointers): the incidence is copied to the
+ * device once, the queries are built one after the other on `stream`, and
+ * the result of each is copied back on a second stream of the call's own
+ * while the next query is built.  Returns when every copy is done: SLG_OK
+ * when every query succeeded, else the first failing query's status (each
+ * query carries its own).  Pinned host arrays make the copies faster.
+ */
+int slg_build_host_many(const slg_hypergraph *h, slg_query *queries,
+                        int32_t count, void *stream);
+
+/*
+ * slg_build_host_csr -- slg_build_host in the compressed row form of
+ * slg_build_csr: row_ptr (HOST int64[R + 1]), out_j and out_w are host
+ * arrays.  Synchronous.  Errors as for slg_build_csr.
+ */
+int slg_build_host_csr(const slg_hypergraph *h, int32_t s, uint32_t flags,
+                       int64_t *row_ptr, int32_t *out_j, int32_t *out_w,
+                       int64_t capacity, int64_t *n_pairs, void *stream);
 
 /*
  * slg_wedges -- W_s, the number of upper-triangle wedges e -> v -> f
@@ -401,6 +460,9 @@ typedef struct slg_stats {
   int64_t max_row_work;    /* largest wedge count of one row */
   float ms_relabel;        /* SLG_RELABEL_*: building the renumbered side */
   float ms_order;          /* SLG_RELABEL_*: caller ids and (i, j) order */
+  int64_t sparse_cycles[5]; /* sparse bin, SM clock cycles summed over CTAs:
+                               row set-up, walk, collect and order the
+                               survivors, emit and clear, staging */
 } slg_stats;
 
 int slg_last_stats(slg_stats *out);

@@ -88,7 +88,16 @@ class _Stats(ctypes.Structure):
                 ("giant_cycles", ctypes.c_int64 * 3),
                 ("max_row_work", ctypes.c_int64),
                 ("ms_relabel", ctypes.c_float),
-                ("ms_order", ctypes.c_float)]
+                ("ms_order", ctypes.c_float),
+                ("sparse_cycles", ctypes.c_int64 * 5)]
+
+
+class _Query(ctypes.Structure):
+    _fields_ = [("s", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("row_ptr", ctypes.c_void_p), ("out_i", ctypes.c_void_p),
+                ("out_j", ctypes.c_void_p), ("out_w", ctypes.c_void_p),
+                ("capacity", ctypes.c_int64), ("n_pairs", ctypes.c_int64),
+                ("status", ctypes.c_int32)]
 
 
 _I64P = ctypes.POINTER(ctypes.c_int64)
@@ -106,6 +115,12 @@ ABI_FUNCTIONS = {
                                       ctypes.c_int64, _I64P, _VP]),
     "slg_build_host": (ctypes.c_int, [_HP, ctypes.c_int32, ctypes.c_uint32, _VP, _VP,
                                       _VP, ctypes.c_int64, _I64P, _VP]),
+    "slg_build_csr": (ctypes.c_int, [_HP, ctypes.c_int32, ctypes.c_uint32, _VP, _VP, _VP,
+                                     ctypes.c_int64, _I64P, _VP]),
+    "slg_build_host_csr": (ctypes.c_int, [_HP, ctypes.c_int32, ctypes.c_uint32, _VP, _VP,
+                                          _VP, ctypes.c_int64, _I64P, _VP]),
+    "slg_build_host_many": (ctypes.c_int, [_HP, ctypes.POINTER(_Query), ctypes.c_int32,
+                                           _VP]),
     "slg_wedges": (ctypes.c_int, [_HP, ctypes.c_int32, ctypes.c_uint32, _I64P, _VP]),
     "slg_row_offsets": (ctypes.c_int, [_HP, ctypes.c_int32, ctypes.c_uint32, _VP, _VP]),
     "slg_last_stats": (ctypes.c_int, [ctypes.POINTER(_Stats)]),
@@ -333,6 +348,72 @@ def build_host(h, s: int, dual=False, unweighted=False, algo="binned",
     return oi[:p], oj[:p], (ow[:p] if ow is not None else None)
 
 
+def build_csr(h: DeviceHypergraph, s: int, dual=False, unweighted=False, algo="binned",
+              capacity=None, out=None, stream=None, tensor=False, prune=True):
+    """L_s in compressed row form: (row_ptr int64 [R + 1], j, w) device
+    tensors; row i's pairs are j[row_ptr[i]:row_ptr[i + 1]] (w None with
+    unweighted=True)."""
+    import torch
+    flags = _flags(dual, unweighted, algo, tensor, None, prune)
+    R = h.rows(dual)
+    if out is None:
+        if capacity is None:
+            capacity = count(h, s, dual, unweighted, algo, stream, tensor)
+        _, oj, ow = _outputs(capacity, unweighted, h.e_off.device)
+        ptr = torch.empty(R + 1, dtype=torch.int64, device=h.e_off.device)
+    else:
+        ptr, oj, ow = out
+    n = ctypes.c_int64(0)
+    rc = load().slg_build_csr(ctypes.byref(h.struct), int(s), flags, ptr.data_ptr(),
+                              oj.data_ptr(), ow.data_ptr() if ow is not None else None,
+                              int(oj.shape[0]), ctypes.byref(n), _stream(stream))
+    if rc != 0:
+        err = SlgError(rc, "slg_build_csr")
+        err.needed = int(n.value)
+        raise err
+    p = int(n.value)
+    return ptr, oj[:p], (ow[:p] if ow is not None else None)
+
+
+def _host_struct(h):
+    def ptr(a):
+        if hasattr(a, "data_ptr"):
+            return a.data_ptr()
+        return a.ctypes.data
+    return _Hypergraph(int(h.m), int(h.n), int(h.e_idx.shape[0]), ptr(h.e_off),
+                       ptr(h.e_idx), ptr(h.v_off), ptr(h.v_idx))
+
+
+def _hptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def build_host_many(h, queries, stream=None):
+    """Several builds of one host hypergraph (slg_build_host_many): the
+    incidence is copied to the device once and each result is copied back
+    while the next is built.  ``queries``: dicts with keys s, dual,
+    unweighted (optional), algo (optional), capacity, and host arrays
+    row_ptr (int64[R + 1]; compressed row form) or out_i, plus out_j, out_w.
+    Returns a list of (status, n_pairs)."""
+    qs = (_Query * len(queries))()
+    for k, q in enumerate(queries):
+        qs[k].s = int(q["s"])
+        qs[k].flags = _flags(q.get("dual", False), q.get("unweighted", False),
+                             q.get("algo", "binned"))
+        qs[k].row_ptr = _hptr(q.get("row_ptr"))
+        qs[k].out_i = _hptr(q.get("out_i"))
+        qs[k].out_j = _hptr(q.get("out_j"))
+        qs[k].out_w = _hptr(q.get("out_w"))
+        qs[k].capacity = int(q["capacity"])
+    st = _host_struct(h)
+    load().slg_build_host_many(ctypes.byref(st), qs, len(queries), _stream(stream))
+    return [(int(q.status), int(q.n_pairs)) for q in qs]
+
+
 def row_offsets(h: DeviceHypergraph, s: int, dual=False, unweighted=False, stream=None,
                 tensor=False, prune=True):
     """int64 CUDA tensor [R + 1]: where each row's pairs start in the
@@ -501,7 +582,7 @@ def last_stats() -> dict:
             "ms_gather": st.ms_gather, "core_rows": st.core_rows, "core_cols": st.core_cols,
             "core_nnz": st.core_nnz, "giant_cycles": list(st.giant_cycles),
             "max_row_work": st.max_row_work, "ms_relabel": st.ms_relabel,
-            "ms_order": st.ms_order}
+            "ms_order": st.ms_order, "sparse_cycles": list(st.sparse_cycles)}
 
 
 def set_core_params(tau_c: int = 64, tau_r: int = 32, min_density: float = 0.02) -> None:

@@ -677,10 +677,17 @@ int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin
   c.smin = smin;
   c.flags = flags;
   c.unweighted = (flags & SLG_UNWEIGHTED) != 0;
+  // Compressed row form (a build with row_ptr_out): the pairs' i is implied
+  // by row_ptr_out, so out_i may be null.
+  const bool rows_form = op == kOpBuild && row_ptr_out != nullptr;
   if (op == kOpBuild) {
     if (capacity < 0) return SLG_ERR_INVALID;
-    if (capacity > 0 && (!out_i || !out_j || (!c.unweighted && !out_w))) return SLG_ERR_INVALID;
+    if (capacity > 0 && ((!rows_form && !out_i) || !out_j || (!c.unweighted && !out_w)))
+      return SLG_ERR_INVALID;
   }
+  if (rows_form && ((flags & SLG_ALGO_MASK) == SLG_ALGO_SPGEMM ||
+                    (flags & (SLG_RELABEL_ASC | SLG_RELABEL_DESC))))
+    return SLG_ERR_UNSUPPORTED;
   c.row_begin = row_begin;
   c.row_end = row_end;
   c.rows = row_end - row_begin;
@@ -799,6 +806,7 @@ int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin
   stats.core_cols = c.core_cols;
   stats.core_nnz = c.core_nnz;
   for (int q = 0; q < 3; ++q) stats.giant_cycles[q] = (int64_t)m.giant_cycles[q];
+  for (int q = 0; q < 5; ++q) stats.sparse_cycles[q] = (int64_t)m.sparse_cycles[q];
   stats.max_row_work = m.max_row_work;
   if (evs.on) {
     stats.profiled = 1;
@@ -934,6 +942,110 @@ cudaError_t enqueue_plan(slg_plan *p, const Bins &bins, cudaStream_t st, int32_t
 #undef PLAN_TRY
 
 }  // namespace
+namespace {
+
+// Device copy of a host hypergraph, enqueued on `st` (buffers from `pool`).
+int upload(const slg_hypergraph *hh, Pool &pool, cudaStream_t st, slg_hypergraph *d) {
+  *d = *hh;
+  int32_t *e_off, *e_idx, *v_off, *v_idx;
+  const size_t m = (size_t)hh->n_edges, n = (size_t)hh->n_vertices, nnz = (size_t)hh->nnz;
+  SLG_TRY(pool.get(&e_off, m + 1));
+  SLG_TRY(pool.get(&v_off, n + 1));
+  SLG_TRY(pool.get(&e_idx, nnz));
+  SLG_TRY(pool.get(&v_idx, nnz));
+  SLG_TRY(cudaMemcpyAsync(e_off, hh->e_off, (m + 1) * 4, cudaMemcpyHostToDevice, st));
+  SLG_TRY(cudaMemcpyAsync(v_off, hh->v_off, (n + 1) * 4, cudaMemcpyHostToDevice, st));
+  if (nnz) {
+    SLG_TRY(cudaMemcpyAsync(e_idx, hh->e_idx, nnz * 4, cudaMemcpyHostToDevice, st));
+    SLG_TRY(cudaMemcpyAsync(v_idx, hh->v_idx, nnz * 4, cudaMemcpyHostToDevice, st));
+  }
+  d->e_off = e_off;
+  d->e_idx = e_idx;
+  d->v_off = v_off;
+  d->v_idx = v_idx;
+  return SLG_OK;
+}
+
+// One query of slg_build_host_many / slg_build_host_csr: device outputs
+// from the library pool on `st`, the build, then the copies back on `cs`
+// once the build is done (the device buffers are released on `cs` after
+// them).  Returns the query's status.
+int host_query(const slg_hypergraph *d, slg_query *q, cudaStream_t st, cudaStream_t cs,
+               cudaEvent_t done) {
+  q->n_pairs = 0;
+  const uint32_t flags = q->flags;
+  if (flags & SLG_ASYNC) return SLG_ERR_INVALID;
+  const bool unweighted = (flags & SLG_UNWEIGHTED) != 0;
+  const bool rows_form = q->row_ptr != nullptr;
+  if (q->capacity < 0) return SLG_ERR_INVALID;
+  if (q->capacity > 0 &&
+      ((!rows_form && !q->out_i) || !q->out_j || (!unweighted && !q->out_w)))
+    return SLG_ERR_INVALID;
+  const int32_t R = (flags & SLG_DUAL) ? d->n_vertices : d->n_edges;
+  cudaMemPool_t mem = lib_pool();
+  void *buf[4] = {nullptr, nullptr, nullptr, nullptr};
+  auto alloc = [&](int k, size_t bytes) {
+    bytes = bytes < 16 ? 16 : bytes;
+    cudaError_t e = mem ? cudaMallocFromPoolAsync(&buf[k], bytes, mem, st)
+                        : cudaMallocAsync(&buf[k], bytes, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      buf[k] = nullptr;
+    }
+    return e;
+  };
+  auto release = [&](cudaStream_t on) {
+    for (void *b : buf)
+      if (b) cudaFreeAsync(b, on);
+  };
+  const size_t cap = (size_t)q->capacity;
+  cudaError_t e = cudaSuccess;
+  if (cap > 0) {
+    if (!rows_form) e = alloc(0, cap * 4);
+    if (e == cudaSuccess) e = alloc(1, cap * 4);
+    if (e == cudaSuccess && !unweighted) e = alloc(2, cap * 4);
+  }
+  if (e == cudaSuccess && rows_form) e = alloc(3, ((size_t)R + 1) * 8);
+  if (e != cudaSuccess) {
+    release(st);
+    return status_of(e);
+  }
+  int64_t pairs = 0;
+  int rc = run(d, q->s, flags, 0, R, kOpBuild, static_cast<int32_t *>(buf[0]),
+               static_cast<int32_t *>(buf[1]), static_cast<int32_t *>(buf[2]), q->capacity,
+               &pairs, st, nullptr, nullptr, static_cast<long long *>(buf[3]));
+  q->n_pairs = pairs;
+  if (rc != SLG_OK) {
+    release(st);
+    return rc;
+  }
+  // the copies back wait for the build (the stream already synchronised
+  // inside run; the event keeps the order explicit for the copy stream)
+  if (cudaEventRecord(done, st) != cudaSuccess || cudaStreamWaitEvent(cs, done, 0) != cudaSuccess) {
+    cudaGetLastError();
+    release(st);
+    return SLG_ERR_CUDA;
+  }
+  const size_t p = (size_t)pairs;
+  cudaError_t c = cudaSuccess;
+  if (rows_form)
+    c = cudaMemcpyAsync(q->row_ptr, buf[3], ((size_t)R + 1) * 8, cudaMemcpyDeviceToHost, cs);
+  if (p > 0) {
+    if (c == cudaSuccess && !rows_form)
+      c = cudaMemcpyAsync(q->out_i, buf[0], p * 4, cudaMemcpyDeviceToHost, cs);
+    if (c == cudaSuccess) c = cudaMemcpyAsync(q->out_j, buf[1], p * 4, cudaMemcpyDeviceToHost, cs);
+    if (c == cudaSuccess && !unweighted)
+      c = cudaMemcpyAsync(q->out_w, buf[2], p * 4, cudaMemcpyDeviceToHost, cs);
+  }
+  release(cs);
+  if (c != cudaSuccess) {
+    cudaGetLastError();
+    return SLG_ERR_CUDA;
+  }
+  return SLG_OK;
+}
+
+}  // namespace
 }  // namespace slg
 
 using namespace slg;
@@ -996,23 +1108,10 @@ int slg_build_host(const slg_hypergraph *hh, int32_t s, uint32_t flags, int32_t 
   if (capacity > 0 && (!out_i || !out_j || (!unweighted && !out_w))) return SLG_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
   Pool pool(st);
-  slg_hypergraph d = *hh;
-  int32_t *e_off, *e_idx, *v_off, *v_idx, *oi = nullptr, *oj = nullptr, *ow = nullptr;
-  const size_t m = (size_t)hh->n_edges, n = (size_t)hh->n_vertices, nnz = (size_t)hh->nnz;
-  SLG_TRY(pool.get(&e_off, m + 1));
-  SLG_TRY(pool.get(&v_off, n + 1));
-  SLG_TRY(pool.get(&e_idx, nnz));
-  SLG_TRY(pool.get(&v_idx, nnz));
-  SLG_TRY(cudaMemcpyAsync(e_off, hh->e_off, (m + 1) * 4, cudaMemcpyHostToDevice, st));
-  SLG_TRY(cudaMemcpyAsync(v_off, hh->v_off, (n + 1) * 4, cudaMemcpyHostToDevice, st));
-  if (nnz) {
-    SLG_TRY(cudaMemcpyAsync(e_idx, hh->e_idx, nnz * 4, cudaMemcpyHostToDevice, st));
-    SLG_TRY(cudaMemcpyAsync(v_idx, hh->v_idx, nnz * 4, cudaMemcpyHostToDevice, st));
-  }
-  d.e_off = e_off;
-  d.e_idx = e_idx;
-  d.v_off = v_off;
-  d.v_idx = v_idx;
+  slg_hypergraph d;
+  rc = upload(hh, pool, st, &d);
+  if (rc != SLG_OK) return rc;
+  int32_t *oi = nullptr, *oj = nullptr, *ow = nullptr;
   if (capacity > 0) {
     SLG_TRY(pool.get(&oi, (size_t)capacity));
     SLG_TRY(pool.get(&oj, (size_t)capacity));
@@ -1031,6 +1130,74 @@ int slg_build_host(const slg_hypergraph *hh, int32_t s, uint32_t flags, int32_t 
   // the device buffers are released after the copies, in stream order
   if (!async) SLG_TRY(cudaStreamSynchronize(st));
   return SLG_OK;
+}
+
+int slg_build_csr(const slg_hypergraph *h, int32_t s, uint32_t flags, int64_t *row_ptr,
+                  int32_t *out_j, int32_t *out_w, int64_t capacity, int64_t *n_pairs,
+                  void *stream) {
+  if (!h || !row_ptr) return SLG_ERR_INVALID;
+  const int32_t R = (flags & SLG_DUAL) ? h->n_vertices : h->n_edges;
+  return run(h, s, flags, 0, R, kOpBuild, nullptr, out_j, out_w, capacity, n_pairs,
+             (cudaStream_t)stream, nullptr, nullptr, reinterpret_cast<long long *>(row_ptr));
+}
+
+int slg_build_host_many(const slg_hypergraph *hh, slg_query *queries, int32_t count,
+                        void *stream) {
+  if (!queries || count < 0) return SLG_ERR_INVALID;
+  for (int32_t k = 0; k < count; ++k) {
+    queries[k].status = SLG_ERR_INVALID;
+    queries[k].n_pairs = 0;
+  }
+  if (count == 0) return SLG_OK;
+  int rc = check_args(hh, 1, 0);
+  if (rc != SLG_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  Pool pool(st);
+  slg_hypergraph d;
+  rc = upload(hh, pool, st, &d);
+  if (rc != SLG_OK) return rc;
+  int dev = 0;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t done = nullptr;
+  SLG_TRY(cudaGetDevice(&dev));
+  SLG_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamDestroy(cs);
+    return SLG_ERR_CUDA;
+  }
+  int first = SLG_OK;
+  for (int32_t k = 0; k < count; ++k) {
+    const int q = host_query(&d, &queries[k], st, cs, done);
+    queries[k].status = q;
+    if (q != SLG_OK && first == SLG_OK) first = q;
+  }
+  // every copy back done; the uploaded input is released on `st` (Pool)
+  const cudaError_t e1 = cudaStreamSynchronize(cs);
+  cudaEventDestroy(done);
+  cudaStreamDestroy(cs);
+  const cudaError_t e2 = cudaStreamSynchronize(st);
+  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    cudaGetLastError();
+    return SLG_ERR_CUDA;
+  }
+  return first;
+}
+
+int slg_build_host_csr(const slg_hypergraph *hh, int32_t s, uint32_t flags, int64_t *row_ptr,
+                       int32_t *out_j, int32_t *out_w, int64_t capacity, int64_t *n_pairs,
+                       void *stream) {
+  if (!row_ptr || !n_pairs) return SLG_ERR_INVALID;
+  slg_query q = {};
+  q.s = s;
+  q.flags = flags;
+  q.row_ptr = row_ptr;
+  q.out_j = out_j;
+  q.out_w = out_w;
+  q.capacity = capacity;
+  const int rc = slg_build_host_many(hh, &q, 1, stream);
+  *n_pairs = q.n_pairs;
+  return rc != SLG_OK ? rc : q.status;
 }
 
 int slg_filter(const int32_t *in_i, const int32_t *in_j, const int32_t *in_w, int64_t n,

@@ -106,7 +106,7 @@ __global__ __launch_bounds__(kNT) void k_gather(int32_t row_begin, int32_t rows,
       raise_error(meta, SLG_ERR_INVALID, kWhereStage);
       continue;
     }
-    out_i[p] = row_begin + r0 + lo;
+    if (out_i) out_i[p] = row_begin + r0 + lo;  // null: compressed row form
     out_j[p] = stage_j[src];
     if (!unweighted) out_w[p] = stage_w[src];
   }

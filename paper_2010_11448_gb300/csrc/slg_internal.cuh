@@ -71,6 +71,7 @@ struct Meta {
   unsigned long long nnz_core;         // incidences of the dense core
   int32_t max_row_work;                // largest work of any row
   unsigned long long giant_cycles[4];  // giant bin: SM cycles in walk, partition, buckets
+  unsigned long long sparse_cycles[5]; // sparse bin: row set-up, walk, collect, emit, staging
 };
 
 // Where a device-side check fired (for error reports).

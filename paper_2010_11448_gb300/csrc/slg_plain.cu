@@ -103,7 +103,7 @@ __global__ __launch_bounds__(kPlainNT) void k_plain(Side sd, int32_t smin, int32
             for (int u = 0; u < 4; ++u)
               if (vals[u] >= smin) {
                 const int64_t o = base + pos++;
-                a.out_i[o] = (int32_t)e;
+                if (a.out_i) a.out_i[o] = (int32_t)e;
                 a.out_j[o] = f0 + 4 * q + u;
                 if (!unweighted) a.out_w[o] = vals[u];
               }

@@ -45,7 +45,7 @@ __device__ __forceinline__ long long reserve(const EmitArgs &a, int32_t e, int32
 __device__ __forceinline__ void put(const EmitArgs &a, long long base, int32_t t, int32_t e,
                                     int32_t f, int32_t c) {
   if (a.mode == kDirect) {
-    a.out_i[base + t] = e;
+    if (a.out_i) a.out_i[base + t] = e;  // null: compressed row form, i implied
     a.out_j[base + t] = f;
     if (!a.unweighted) a.out_w[base + t] = c;
   } else {
@@ -989,17 +989,32 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
 // later windows read them from there instead of walking again, and its bits
 // are cleared from them instead of over the whole window.
 
-constexpr int kSpNT = 1024;
-constexpr int kSpWinLog = 20;                    // ids per window (bitmap 128 KB)
+#ifndef SLG_SP_NT
+#define SLG_SP_NT 1024
+#endif
+#ifndef SLG_SP_WINLOG
+#define SLG_SP_WINLOG 20
+#endif
+#ifndef SLG_SP_LGT
+#define SLG_SP_LGT 12
+#endif
+#ifndef SLG_SP_CACHE
+#define SLG_SP_CACHE 8192
+#endif
+#ifndef SLG_SP_MINB
+#define SLG_SP_MINB 1
+#endif
+constexpr int kSpNT = SLG_SP_NT;
+constexpr int kSpWinLog = SLG_SP_WINLOG;         // ids per window (bitmap 2^(winlog-3) bytes)
 constexpr int kSpWords = 1 << (kSpWinLog - 5);
-constexpr int kSpCache = 8192;                   // far ends kept of a small row
-constexpr int kSpT = 4096;                       // repeats table slots (32 KB)
-constexpr int kSpLgT = 12;
+constexpr int kSpCache = SLG_SP_CACHE;           // far ends kept of a small row
+constexpr int kSpLgT = SLG_SP_LGT;
+constexpr int kSpT = 1 << kSpLgT;                // repeats table slots
 constexpr int kSpClaims = kSpT / 2;              // distinct repeated far ends per window
 constexpr int kSpList = kSpClaims;               // survivors per window (<= claims)
 constexpr int kSpQ = kSpList / kSpNT;
 constexpr int kSpG = 6;                          // wedges per thread per walk step
-static_assert(kSpT == 1 << kSpLgT && kSpQ * kSpNT >= kSpList, "sparse bin geometry");
+static_assert(kSpQ >= 1 && kSpQ * kSpNT >= kSpList, "sparse bin geometry");
 
 // [s_base 8][s_flag 8: overflow, claims][s_row 4][pad 12][bitmap kSpWords x 4]
 // [table kSpT x 8][cache kSpCache x 4][s_beg NT][s_pref NT+1][ws NT/32+1]
@@ -1048,7 +1063,7 @@ __device__ __forceinline__ void sparse_repeat(unsigned long long *tab, int32_t f
   *(volatile int32_t *)s_flag = 1;
 }
 
-__global__ __launch_bounds__(kSpNT, 1) void k_walk_sparse(Walk w, const int32_t *__restrict__ rows,
+__global__ __launch_bounds__(kSpNT, SLG_SP_MINB) void k_walk_sparse(Walk w, const int32_t *__restrict__ rows,
                                                           EmitArgs a, int32_t *__restrict__ scratch,
                                                           long long scratch_stride, int32_t R,
                                                           int32_t list_len) {
@@ -1084,7 +1099,10 @@ __global__ __launch_bounds__(kSpNT, 1) void k_walk_sparse(Walk w, const int32_t 
   const unsigned nhuge = meta->sparse_huge;
   const bool unweighted = a.unweighted != 0;
   const bool emit = a.mode != kCount;
+  // SM cycles of the CTA's first thread: row set-up, walk, collect, emit, staging
+  long long cyc[5] = {0, 0, 0, 0, 0};
   for (;;) {
+    long long t0 = clock64();
     __syncthreads();
     if (threadIdx.x == 0) {
       const unsigned t = atomicAdd(&meta->sparse_ticket, 1u);
@@ -1108,6 +1126,11 @@ __global__ __launch_bounds__(kSpNT, 1) void k_walk_sparse(Walk w, const int32_t 
     int32_t out = 0;  // pairs of the row so far
     int32_t width = 1 << kSpWinLog;
     bool first = true;
+    {
+      const long long t1 = clock64();
+      cyc[0] += t1 - t0;
+      t0 = t1;
+    }
     for (int32_t wlo = f_lo; wlo < R;) {
       const int32_t whi = (R - wlo > width) ? wlo + width : R;
       auto visit = [&](int32_t f) {
@@ -1130,10 +1153,20 @@ __global__ __launch_bounds__(kSpNT, 1) void k_walk_sparse(Walk w, const int32_t 
       }
       first = false;
       __syncthreads();  // every insert done
+      {
+        const long long t1 = clock64();
+        cyc[1] += t1 - t0;
+        t0 = t1;
+      }
       const bool overflow = s_flag[0] != 0;
       int32_t n = 0, at = 0, used = 0;
       if (!overflow)  // survivors, table cleared, sorted at tab[at, at + n)
         n = table_collect_list<kSpNT, kSpQ>(tab, kSpT, sl, emit, &at, &used);
+      {
+        const long long t1 = clock64();
+        cyc[2] += t1 - t0;
+        t0 = t1;
+      }
       // bits of the window back to zero
       if (cached) {
         __syncthreads();
@@ -1182,6 +1215,11 @@ __global__ __launch_bounds__(kSpNT, 1) void k_walk_sparse(Walk w, const int32_t 
       out += n;
       table_reset_front<kSpNT>(tab, used);
       if (threadIdx.x == 0) s_flag[1] = 0;
+      {
+        const long long t1 = clock64();
+        cyc[3] += t1 - t0;
+        t0 = t1;
+      }
       wlo = whi;
       if (width < (1 << kSpWinLog)) width <<= 1;
     }
@@ -1195,7 +1233,10 @@ __global__ __launch_bounds__(kSpNT, 1) void k_walk_sparse(Walk w, const int32_t 
           if (!unweighted) a.stage_w[b + i] = tw[i];
         }
     }
+    cyc[4] += clock64() - t0;
   }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 5; ++q) atomicAdd(&meta->sparse_cycles[q], (unsigned long long)cyc[q]);
 }
 
 // --------------------------------------------------------------- launch --
