@@ -186,12 +186,91 @@ struct Walk {
 
 // CTA-wide walker.  Shared scratch: s_beg[NT], s_pref[NT + 1], ws[NT/32 + 1].
 // fn(f, i) receives every wedge's far end f and its index i in the row's
-// flattened wedge list (0 .. work-1).  Each thread takes G consecutive
-// wedges per step, found by one binary search over the prefix sums.
+// flattened wedge list (0 .. work-1).
+//
+// Lane layout (the default): a batch's flattened wedges are cut into chunks
+// of 32 G; warp w takes chunks w, w + NT/32, ...; in a chunk, lane l takes
+// wedges c0 + 32 g + l (g < G), so every warp-wide load of far ends reads
+// 32 consecutive wedges (a few tails) and is coalesced.  The chunk's first
+// incidence is found by one binary search (the same address in every lane);
+// each lane then steps forward over the incidences its wedges cross.
+#ifndef SLG_WALK_LANES
+#define SLG_WALK_LANES 1
+#endif
+template <int NT, int G, bool kBatched = false, class Fn>
+__device__ __forceinline__ void cta_walk_lanes(const Walk &w, int32_t k0, int32_t k1,
+                                               int32_t *s_beg, int32_t *s_pref, int32_t *ws,
+                                               Fn &&fn) {
+  const int32_t lane = (int32_t)(threadIdx.x & 31);
+  int32_t done = 0;  // wedges of earlier batches
+  for (int32_t base = k0; base < k1; base += NT) {
+    const int32_t k = base + (int32_t)threadIdx.x;
+    int32_t b = 0, len = 0;
+    if (k < k1) {
+      b = __ldg(w.tail_beg + k);
+      len = __ldg(w.tail_end + k) - b;
+    }
+    int32_t total;
+    const int32_t inc = block_inclusive_scan<NT>(len, ws, &total);
+    s_beg[threadIdx.x] = b;
+    s_pref[threadIdx.x + 1] = inc;
+    if (threadIdx.x == 0) s_pref[0] = 0;
+    __syncthreads();
+    for (int32_t c0 = (int32_t)(threadIdx.x >> 5) * 32 * G; c0 < total; c0 += NT * G) {
+      int32_t lo = 0, hi = NT;  // invariant: s_pref[lo] <= c0 < s_pref[hi]
+      while (hi - lo > 1) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (s_pref[mid] <= c0) lo = mid;
+        else hi = mid;
+      }
+      int32_t src[G];
+      int32_t j = lo;
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int32_t i = c0 + 32 * g + lane;
+        src[g] = -1;
+        if (i < total) {
+          while (s_pref[j + 1] <= i) ++j;
+          src[g] = s_beg[j] + (i - s_pref[j]);
+        }
+      }
+      int32_t f[G];
+#pragma unroll
+      for (int g = 0; g < G; ++g) f[g] = src[g] >= 0 ? __ldg(w.c_idx_s + src[g]) : -1;
+      if constexpr (kBatched) {
+        fn(f, done + c0 + lane);  // f[g] < 0: no wedge; index of f[g]: + 32 g
+      } else {
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+          if (src[g] >= 0) fn(f[g], done + c0 + 32 * g + lane);
+      }
+    }
+    done += total;
+    __syncthreads();
+  }
+}
+
+// The lane-layout walker handing each thread's G far ends of a step to
+// fn(f[G], i0) at once (f[g] = -1 where there is no wedge; the index of
+// f[g] is i0 + 32 g), so that fn can issue its shared-memory updates for
+// all of them before using any result.
+template <int NT, int G, class Fn>
+__device__ __forceinline__ void cta_walk_batched(const Walk &w, int32_t k0, int32_t k1,
+                                                 int32_t *s_beg, int32_t *s_pref, int32_t *ws,
+                                                 Fn &&fn) {
+  cta_walk_lanes<NT, G, true>(w, k0, k1, s_beg, s_pref, ws, fn);
+}
+
+// Thread layout: each thread takes G consecutive wedges per step, found by
+// one binary search over the prefix sums.
 template <int NT, int G, class Fn>
 __device__ __forceinline__ void cta_walk(const Walk &w, int32_t k0, int32_t k1,
                                          int32_t *s_beg, int32_t *s_pref, int32_t *ws,
                                          Fn &&fn) {
+#if SLG_WALK_LANES
+  cta_walk_lanes<NT, G>(w, k0, k1, s_beg, s_pref, ws, fn);
+  return;
+#endif
   int32_t done = 0;  // wedges of earlier batches
   for (int32_t base = k0; base < k1; base += NT) {
     const int32_t k = base + (int32_t)threadIdx.x;

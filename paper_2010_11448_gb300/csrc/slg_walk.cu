@@ -977,23 +977,28 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
 // SM) keeps one bit per id of a window of the span: the first wedge to f sets
 // f's bit (one shared atomicOr) and does nothing else; only a wedge that finds
 // the bit already set -- a repeat -- goes to a small shared hash table, whose
-// count word holds the repeats of f minus one.  |e ∩ f| = repeats + 1, and f
-// is listed as a survivor when that reaches s, as in the other bins.
+// count word holds the repeats of f minus one, so |e ∩ f| = count word + 2.
+// When a count reaches s, f's bit in a summary bitmap (one bit per 32 ids)
+// is set.
+//
+// Emission needs no sort: thread t owns 1024 consecutive ids of the window
+// (one summary word, 32 words of the seen bitmap).  It looks up the seen ids
+// of its summary-marked words in the table and counts its pairs; a block scan
+// places every thread's pairs, and a second pass writes them, in ascending f,
+// and clears the thread's own bits.  No survivor list, no single shared
+// counter: the only shared atomics are the per-wedge bit, the repeats and the
+// summary bits.
 //
 // Window: 2^kSpWinLog ids of the span [f_lo, R), processed in ascending
-// order, so the row's output comes out sorted.  If a window's distinct
-// repeated far ends exceed what the table holds (kSpClaims), the window is
-// given up -- its bits and table cleared -- and redone at half the width (a
-// window of at most kSpClaims ids can never overflow).  The first walk of a
-// row of at most kSpCache wedges keeps every far end in shared memory; its
-// later windows read them from there instead of walking again, and its bits
-// are cleared from them instead of over the whole window.
+// order, so the row's output comes out sorted.  If the repeats table of a
+// window gets too full (a probe sequence longer than kSpMaxProbe), the window
+// is given up -- its bits cleared -- and redone at half the width; a window
+// of at most kSpT / 4 ids can never overflow.  The first walk of a row of at
+// most kSpCache wedges keeps every far end in shared memory, so that its
+// later windows read them from there instead of walking again.
 
 #ifndef SLG_SP_NT
 #define SLG_SP_NT 1024
-#endif
-#ifndef SLG_SP_WINLOG
-#define SLG_SP_WINLOG 20
 #endif
 #ifndef SLG_SP_LGT
 #define SLG_SP_LGT 12
@@ -1005,125 +1010,125 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
 #define SLG_SP_MINB 1
 #endif
 constexpr int kSpNT = SLG_SP_NT;
-constexpr int kSpWinLog = SLG_SP_WINLOG;         // ids per window (bitmap 2^(winlog-3) bytes)
-constexpr int kSpWords = 1 << (kSpWinLog - 5);
-constexpr int kSpCache = SLG_SP_CACHE;           // far ends kept of a small row
+constexpr int kSpWinLog = 31 - __builtin_clz(kSpNT) + 10;  // 1024 ids per thread
+constexpr int kSpWords = 1 << (kSpWinLog - 5);              // seen bitmap words
+constexpr int kSpCache = SLG_SP_CACHE;                      // far ends kept of a small row
 constexpr int kSpLgT = SLG_SP_LGT;
-constexpr int kSpT = 1 << kSpLgT;                // repeats table slots
-constexpr int kSpClaims = kSpT / 2;              // distinct repeated far ends per window
-constexpr int kSpList = kSpClaims;               // survivors per window (<= claims)
-constexpr int kSpQ = kSpList / kSpNT;
-constexpr int kSpG = 6;                          // wedges per thread per walk step
-static_assert(kSpQ >= 1 && kSpQ * kSpNT >= kSpList, "sparse bin geometry");
+constexpr int kSpT = 1 << kSpLgT;                           // repeats table slots
+constexpr int kSpMaxProbe = 48;
+#ifndef SLG_SP_G
+#define SLG_SP_G 6
+#endif
+constexpr int kSpG = SLG_SP_G;                              // wedges per thread per walk step
+static_assert(kSpWords / 32 == kSpNT, "one summary word per thread");
 
-// [s_base 8][s_flag 8: overflow, claims][s_row 4][pad 12][bitmap kSpWords x 4]
-// [table kSpT x 8][cache kSpCache x 4][s_beg NT][s_pref NT+1][ws NT/32+1]
-// [list kSpList][list count 1]
+// [s_base 8][s_flag 4: overflow][s_row 4][pad 16][seen bitmap kSpWords x 4]
+// [table kSpT x 8][summary kSpNT x 4][cache kSpCache x 4][s_beg NT]
+// [s_pref NT+1][ws NT/32+1]
 constexpr size_t sparse_smem() {
-  return 32 + (size_t)kSpWords * 4 + (size_t)kSpT * 8 + (size_t)kSpCache * 4 +
-         (size_t)(2 * kSpNT + 1 + kSpNT / 32 + 1) * 4 + (size_t)(kSpList + 1) * 4;
+  return 32 + (size_t)kSpWords * 4 + (size_t)kSpT * 8 + (size_t)kSpNT * 4 +
+         (size_t)kSpCache * 4 + (size_t)(2 * kSpNT + 1 + kSpNT / 32 + 1) * 4;
 }
 
 // A repeat of far end f (its bit was already set).  The first repeat claims
-// f's slot (32-bit CAS on the key word; the count word stays 0 = one
-// repeat), later ones add to the count word.  Unweighted: a pair that reached
-// s is not counted further.  Once the window has overflowed nothing is
-// inserted (the window will be redone).
-__device__ __forceinline__ void sparse_repeat(unsigned long long *tab, int32_t f, int32_t smin,
-                                              bool unweighted, int32_t *s_flag,
-                                              const SurvList &sl) {
-  if (*(volatile int32_t *)s_flag) return;
+// f's slot (32-bit CAS on the key word; the count word stays 0: |e ∩ f| = 2),
+// later ones add to the count word.  Unweighted: a pair that reached s is
+// not counted further.  Returns true when this wedge brought |e ∩ f| to s.
+// A probe sequence longer than max_probe marks the window as overflowed
+// (it will be redone); once marked, nothing more is inserted.
+__device__ __forceinline__ bool sparse_repeat(unsigned long long *tab, int32_t f, int32_t smin,
+                                              bool unweighted, int32_t *s_ovf,
+                                              int max_probe) {
+  if (*(volatile int32_t *)s_ovf) return false;
   uint32_t h = ((uint32_t)f * 0x9E3779B1u) >> (32 - kSpLgT);
-  for (int probe = 0; probe < kSpT; ++probe) {
+  for (int probe = 0; probe < max_probe; ++probe) {
     uint32_t *cw = count_word(tab, h);
     const uint32_t k = atomicCAS(cw + 1, 0xFFFFFFFFu, (uint32_t)f);
-    if (k == 0xFFFFFFFFu) {  // first repeat: |e ∩ f| = 2 so far
-      if (atomicAdd(s_flag + 1, 1) >= kSpClaims) {
-        *(volatile int32_t *)s_flag = 1;  // too many: the window is redone narrower
-        return;
-      }
-      if (smin <= 2) {
-        const int32_t p = atomicAdd(sl.n, 1);
-        if (p < sl.cap) sl.slot[p] = (int32_t)h;
-      }
-      return;
-    }
-    if (k == (uint32_t)f) {  // count word = repeats - 1, |e ∩ f| = count word + 2
-      if (unweighted && (int32_t)*(volatile uint32_t *)cw + 2 >= smin) return;
+    if (k == 0xFFFFFFFFu) return smin <= 2;  // first repeat: |e ∩ f| = 2
+    if (k == (uint32_t)f) {
+      if (unweighted && (int32_t)*(volatile uint32_t *)cw + 2 >= smin) return false;
       const int32_t old = (int32_t)atomicAdd(cw, 1u);
-      if (old + 2 < smin && old + 3 >= smin) {
-        const int32_t p = atomicAdd(sl.n, 1);
-        if (p < sl.cap) sl.slot[p] = (int32_t)h;
-      }
-      return;
+      return old + 2 < smin && old + 3 >= smin;
     }
     h = (h + 1) & (kSpT - 1);
   }
-  // unreachable: claims stop at kSpClaims + kSpNT < kSpT, so a free slot exists
-  *(volatile int32_t *)s_flag = 1;
+  *(volatile int32_t *)s_ovf = 1;
+  return false;
 }
 
-__global__ __launch_bounds__(kSpNT, SLG_SP_MINB) void k_walk_sparse(Walk w, const int32_t *__restrict__ rows,
-                                                          EmitArgs a, int32_t *__restrict__ scratch,
-                                                          long long scratch_stride, int32_t R,
-                                                          int32_t list_len) {
+// |e ∩ f| of a seen far end f: 2 + its count word if f repeated, else 1.
+__device__ __forceinline__ int32_t sparse_weight(const unsigned long long *tab, int32_t f) {
+  uint32_t h = ((uint32_t)f * 0x9E3779B1u) >> (32 - kSpLgT);
+  for (int probe = 0; probe < kSpT; ++probe) {
+    const unsigned long long x = tab[h];
+    const uint32_t k = (uint32_t)(x >> 32);
+    if (k == (uint32_t)f) return (int32_t)(uint32_t)x + 2;
+    if (k == 0xFFFFFFFFu) break;
+    h = (h + 1) & (kSpT - 1);
+  }
+  return 1;
+}
+
+__global__ __launch_bounds__(kSpNT, SLG_SP_MINB) void k_walk_sparse(
+    Walk w, const int32_t *__restrict__ rows, EmitArgs a, int32_t *__restrict__ scratch,
+    long long scratch_stride, int32_t R, int32_t list_len) {
   Meta *meta = a.meta;
   if (meta->err) return;
   extern __shared__ __align__(16) unsigned char smem[];
   long long *s_base = reinterpret_cast<long long *>(smem);
-  int32_t *s_flag = reinterpret_cast<int32_t *>(smem + 8);  // [0] overflow, [1] claims
-  int32_t *s_row = reinterpret_cast<int32_t *>(smem + 16);
+  int32_t *s_ovf = reinterpret_cast<int32_t *>(smem + 8);
+  int32_t *s_row = reinterpret_cast<int32_t *>(smem + 12);
   uint32_t *bm = reinterpret_cast<uint32_t *>(smem + 32);
   unsigned long long *tab = reinterpret_cast<unsigned long long *>(bm + kSpWords);
-  int32_t *cache = reinterpret_cast<int32_t *>(tab + kSpT);
+  uint32_t *summ = reinterpret_cast<uint32_t *>(tab + kSpT);
+  int32_t *cache = reinterpret_cast<int32_t *>(summ + kSpNT);
   int32_t *s_beg = cache + kSpCache;
   int32_t *s_pref = s_beg + kSpNT;
   int32_t *ws = s_pref + kSpNT + 1;
-  const SurvList sl = {ws + kSpNT / 32 + 1, ws + kSpNT / 32 + 1 + kSpList, kSpList};
-  // per-CTA global scratch: the row's staged pairs, j then w (<= work / 2 each)
+  // per-CTA global scratch: the pairs of a row spread over several windows,
+  // j then w (<= work / 2 each)
   const long long half = scratch_stride / 2;
   int32_t *tj = scratch ? scratch + (long long)blockIdx.x * scratch_stride : nullptr;
   int32_t *tw = tj ? tj + half : nullptr;
+  const int32_t tid = (int32_t)threadIdx.x;
 
   {
     uint4 *b4 = reinterpret_cast<uint4 *>(bm);
-    for (int i = threadIdx.x; i < kSpWords / 4; i += kSpNT) b4[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < kSpWords / 4; i += kSpNT) b4[i] = make_uint4(0, 0, 0, 0);
   }
-  for (int i = threadIdx.x; i < kSpT; i += kSpNT) tab[i] = kEmpty64;
-  if (threadIdx.x == 0) {
-    *sl.n = 0;
-    s_flag[0] = 0;
-    s_flag[1] = 0;
-  }
+  summ[tid] = 0u;
   const unsigned nrows = (unsigned)meta->rows_bin[kBinSparse];
   const unsigned nhuge = meta->sparse_huge;
+  auto row_of = [&](unsigned t) -> int32_t {
+    return t >= nrows ? -1 : rows[t < nhuge ? t : list_len - 1 - (t - nhuge)];
+  };
+  // rows above kGiantHugeWork first; the next row's ticket is taken while a
+  // row is processed
+  if (tid == 0) *s_row = row_of(atomicAdd(&meta->sparse_ticket, 1u));
   const bool unweighted = a.unweighted != 0;
-  const bool emit = a.mode != kCount;
-  // SM cycles of the CTA's first thread: row set-up, walk, collect, emit, staging
+  // SM cycles of the CTA's first thread: row set-up, walk, count and place,
+  // write and clear, row end
   long long cyc[5] = {0, 0, 0, 0, 0};
   for (;;) {
     long long t0 = clock64();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const unsigned t = atomicAdd(&meta->sparse_ticket, 1u);
-      s_flag[0] = 0;  // overflow
-      s_flag[1] = 0;  // claims of the window
-      *s_row = t >= nrows ? -1 : rows[t < nhuge ? t : list_len - 1 - (t - nhuge)];
-    }
-    __syncthreads();
+    __syncthreads();  // s_row set; the previous row's bits, summary and scratch copy done
     const int32_t e = *s_row;
     if (e < 0) break;
+    unsigned t_next = 0;
+    if (tid == 0) t_next = atomicAdd(&meta->sparse_ticket, 1u);  // used at the row's end
     const int32_t smin = s_of(a.row_s, a.smin, e);
     const int32_t f_lo = a.full_rows ? 0 : e + 1;
     const int32_t work = a.row_work[e - a.row_begin];
+    const int32_t k0 = w.r_off[e], k1 = w.r_off[e + 1];
     const bool cached = work <= kSpCache;
     if (a.mode == kStage && (long long)work / 2 > half) {  // scratch sized by the largest row
-      if (threadIdx.x == 0) raise_error(meta, SLG_ERR_INVALID, kWhereGiant);
+      if (tid == 0) raise_error(meta, SLG_ERR_INVALID, kWhereGiant);
       break;
     }
-    long long base = -1;
-    if (a.mode == kDirect) base = a.row_ptr[e - a.row_begin];
-    int32_t out = 0;  // pairs of the row so far
+    long long base = a.mode == kDirect ? a.row_ptr[e - a.row_begin] : -1;
+    int32_t out = 0;             // pairs of the row so far
+    bool placed = false;         // STAGE: the row's pairs went straight to the staging area
+    bool failed = false;
     int32_t width = 1 << kSpWinLog;
     bool first = true;
     {
@@ -1133,23 +1138,48 @@ __global__ __launch_bounds__(kSpNT, SLG_SP_MINB) void k_walk_sparse(Walk w, cons
     }
     for (int32_t wlo = f_lo; wlo < R;) {
       const int32_t whi = (R - wlo > width) ? wlo + width : R;
-      auto visit = [&](int32_t f) {
-        if (f >= wlo && f < whi) {
-          const uint32_t b = (uint32_t)(f - wlo), m = 1u << (b & 31);
-          if (atomicOr(bm + (b >> 5), m) & m)
-            sparse_repeat(tab, f, smin, unweighted, s_flag, sl);
+      const int max_probe = width <= kSpT / 4 ? kSpT : kSpMaxProbe;
+      __syncthreads();  // the previous window's look-ups done
+      {
+        ulonglong2 *t2 = reinterpret_cast<ulonglong2 *>(tab);
+        const ulonglong2 em = make_ulonglong2(kEmpty64, kEmpty64);
+        for (int i = tid; i < kSpT / 2; i += kSpNT) t2[i] = em;
+        if (tid == 0) *s_ovf = 0;
+      }
+      auto visit = [&](int32_t f, uint32_t bo, uint32_t mo) {
+        if ((bo & mo) && sparse_repeat(tab, f, smin, unweighted, s_ovf, max_probe)) {
+          const uint32_t b = (uint32_t)(f - wlo);
+          atomicOr(summ + (b >> 10), 1u << ((b >> 5) & 31));
         }
       };
-      __syncthreads();  // flags reset, bits and table clear
       if (first || !cached) {
         const bool keep = first && cached;
-        cta_walk<kSpNT, kSpG>(w, w.r_off[e], w.r_off[e + 1], s_beg, s_pref, ws,
-                              [&](int32_t f, int32_t i) {
-                                if (keep) cache[i] = f;
-                                visit(f);
-                              });
+        // (the walk's scan barriers order the table clear before any insert)
+        // every bit of a step is set before any result is looked at, so a
+        // thread's G shared atomics are in flight together
+        cta_walk_batched<kSpNT, kSpG>(
+            w, k0, k1, s_beg, s_pref, ws, [&](const int32_t(&f)[kSpG], int32_t i0) {
+              uint32_t old[kSpG], m[kSpG];
+#pragma unroll
+              for (int g = 0; g < kSpG; ++g) {
+                if (keep && f[g] >= 0) cache[i0 + 32 * g] = f[g];
+                const bool in = f[g] >= wlo && f[g] < whi;  // f < 0: no wedge
+                const uint32_t b = (uint32_t)(f[g] - wlo);
+                m[g] = in ? 1u << (b & 31) : 0u;
+                old[g] = in ? atomicOr(bm + (b >> 5), m[g]) : 0u;
+              }
+#pragma unroll
+              for (int g = 0; g < kSpG; ++g) visit(f[g], old[g], m[g]);
+            });
       } else {
-        for (int32_t i = threadIdx.x; i < work; i += kSpNT) visit(cache[i]);
+        __syncthreads();  // table clear before the inserts
+        for (int32_t i = tid; i < work; i += kSpNT) {
+          const int32_t f = cache[i];
+          if (f >= wlo && f < whi) {
+            const uint32_t b = (uint32_t)(f - wlo), m = 1u << (b & 31);
+            visit(f, atomicOr(bm + (b >> 5), m), m);
+          }
+        }
       }
       first = false;
       __syncthreads();  // every insert done
@@ -1158,63 +1188,85 @@ __global__ __launch_bounds__(kSpNT, SLG_SP_MINB) void k_walk_sparse(Walk w, cons
         cyc[1] += t1 - t0;
         t0 = t1;
       }
-      const bool overflow = s_flag[0] != 0;
-      int32_t n = 0, at = 0, used = 0;
-      if (!overflow)  // survivors, table cleared, sorted at tab[at, at + n)
-        n = table_collect_list<kSpNT, kSpQ>(tab, kSpT, sl, emit, &at, &used);
+      // thread t's ids: [wlo + 1024 t, + 1024); its seen words [32 t, 32 t + 32)
+      const int32_t nw = (int32_t)(((uint32_t)(whi - wlo) + 31u) >> 5);  // words in use
+      const int32_t w0 = tid * 32;
+      auto clear_own = [&]() {
+        if (w0 < nw) {
+          uint4 *b4 = reinterpret_cast<uint4 *>(bm + w0);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) b4[q] = make_uint4(0, 0, 0, 0);
+          summ[tid] = 0u;
+        }
+      };
+      if (*s_ovf) {  // uniform: read after the barrier
+        clear_own();
+        if (width <= kSpT / 4) {  // cannot overflow: a bound was broken
+          if (tid == 0) raise_error(meta, SLG_ERR_INVALID, kWhereHash);
+          failed = true;
+          break;
+        }
+        width >>= 1;  // retry the same ids, narrower
+        continue;
+      }
+      // pass 1: this thread's pairs
+      const uint32_t sw = w0 < nw ? summ[tid] : 0u;
+      int32_t c = 0;
+      for (uint32_t q = sw; q; q &= q - 1) {
+        const int32_t wi = w0 + __ffs(q) - 1;
+        for (uint32_t x = bm[wi]; x; x &= x - 1) {
+          const int32_t f = wlo + wi * 32 + __ffs(x) - 1;
+          c += sparse_weight(tab, f) >= smin;
+        }
+      }
+      int32_t n;
+      const int32_t inc = block_inclusive_scan<kSpNT>(c, ws, &n);
+      // where the window's pairs go: the row's own place in the staging area
+      // when this window holds all of them, else the CTA's scratch
+      const bool to_stage = a.mode == kStage && out == 0 && whi == R;
+      if (to_stage) {
+        if (tid == 0) *s_base = reserve(a, e, n, kBinSparse);
+        __syncthreads();
+        base = *s_base;
+        placed = true;
+      }
+      if (a.mode == kStage && !to_stage && out + n > half) {
+        if (tid == 0) raise_error(meta, SLG_ERR_INVALID, kWhereGiant);
+        clear_own();
+        failed = true;
+        break;
+      }
       {
         const long long t1 = clock64();
         cyc[2] += t1 - t0;
         t0 = t1;
       }
-      // bits of the window back to zero
-      if (cached) {
-        __syncthreads();
-        for (int32_t i = threadIdx.x; i < work; i += kSpNT) {
-          const int32_t f = cache[i];
-          if (f >= wlo && f < whi) bm[(uint32_t)(f - wlo) >> 5] = 0u;
-        }
-      } else {
-        uint4 *b4 = reinterpret_cast<uint4 *>(bm);
-        const int32_t nw4 = (int32_t)((((uint32_t)(whi - wlo) + 31u) >> 5) + 3) >> 2;
-        for (int32_t i = threadIdx.x; i < nw4; i += kSpNT) b4[i] = make_uint4(0, 0, 0, 0);
-      }
-      if (overflow) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < kSpT; i += kSpNT) tab[i] = kEmpty64;
-        if (threadIdx.x == 0) {
-          *sl.n = 0;
-          s_flag[0] = 0;
-          s_flag[1] = 0;
-        }
-        if (width <= kSpClaims) {  // cannot overflow: a bound was broken
-          if (threadIdx.x == 0) raise_error(meta, SLG_ERR_INVALID, kWhereHash);
-          break;
-        }
-        width >>= 1;  // retry the same ids, narrower (uniform decision)
-        continue;
-      }
-      if (a.mode == kStage && out + n > half) {
-        if (threadIdx.x == 0) raise_error(meta, SLG_ERR_INVALID, kWhereGiant);
-        table_reset_front<kSpNT>(tab, used);
-        break;
-      }
-      if (emit && n > 0) {
-        for (int32_t i = threadIdx.x; i < n; i += kSpNT) {
-          const unsigned long long x = tab[at + i];
-          // table_collect_list added one to the count word: repeats; + 1
-          const int32_t f = (int32_t)(x >> 32), c = (int32_t)(uint32_t)x + 1;
-          if (a.mode == kDirect) {
-            put(a, base, out + i, e, f, c);
-          } else {
-            tj[out + i] = f;
-            if (!unweighted) tw[out + i] = c;
+      // pass 2: write this thread's pairs in ascending f; clear its bits
+      if (c > 0 && a.mode != kCount) {
+        int32_t p = out + inc - c;
+        for (uint32_t q = sw; q; q &= q - 1) {
+          const int32_t wi = w0 + __ffs(q) - 1;
+          for (uint32_t x = bm[wi]; x; x &= x - 1) {
+            const int32_t f = wlo + wi * 32 + __ffs(x) - 1;
+            const int32_t wt = sparse_weight(tab, f);
+            if (wt < smin) continue;
+            if (a.mode == kDirect) {
+              put(a, base, p, e, f, wt);
+            } else if (to_stage) {
+              if (base >= 0) {
+                a.stage_j[base + p] = f;
+                if (!unweighted) a.stage_w[base + p] = wt;
+              }
+            } else {
+              tj[p] = f;
+              if (!unweighted) tw[p] = wt;
+            }
+            ++p;
           }
         }
       }
+      clear_own();
       out += n;
-      table_reset_front<kSpNT>(tab, used);
-      if (threadIdx.x == 0) s_flag[1] = 0;
       {
         const long long t1 = clock64();
         cyc[3] += t1 - t0;
@@ -1223,19 +1275,23 @@ __global__ __launch_bounds__(kSpNT, SLG_SP_MINB) void k_walk_sparse(Walk w, cons
       wlo = whi;
       if (width < (1 << kSpWinLog)) width <<= 1;
     }
-    if (threadIdx.x == 0) *s_base = reserve(a, e, out, kBinSparse);
-    __syncthreads();
-    if (a.mode == kStage) {
-      const long long b = *s_base;
-      if (b >= 0)
-        for (int32_t i = threadIdx.x; i < out; i += kSpNT) {
-          a.stage_j[b + i] = tj[i];
-          if (!unweighted) a.stage_w[b + i] = tw[i];
-        }
+    if (failed) break;
+    if (!placed) {
+      if (tid == 0) *s_base = reserve(a, e, out, kBinSparse);
+      __syncthreads();
+      if (a.mode == kStage) {
+        const long long b = *s_base;
+        if (b >= 0)
+          for (int32_t i = tid; i < out; i += kSpNT) {
+            a.stage_j[b + i] = tj[i];
+            if (!unweighted) a.stage_w[b + i] = tw[i];
+          }
+      }
     }
+    if (tid == 0) *s_row = row_of(t_next);
     cyc[4] += clock64() - t0;
   }
-  if (threadIdx.x == 0)
+  if (tid == 0)
     for (int q = 0; q < 5; ++q) atomicAdd(&meta->sparse_cycles[q], (unsigned long long)cyc[q]);
 }
 

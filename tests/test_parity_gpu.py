@@ -1,5 +1,7 @@
 """CUDA path vs the CPU oracle, element by element (bit-exact: every count is
 an exact integer).  All calls go through the C ABI via the thin binding."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -352,3 +354,88 @@ def test_giant_rows_beyond_one_super_chunk():
     want = oracle.canonical(*oracle.line_graph(m, n_, off, idx, 1, rows=rows, threads=16))
     assert np.array_equal(sel, want)
     assert got.shape[0] == slg.count(dh, 1, dual=True)
+
+
+# ------------------------------------------------ compressed row form (CSR) --
+
+def _csr_to_triples(ptr, j, w):
+    ptr = np.asarray(ptr, np.int64)
+    i = np.repeat(np.arange(ptr.shape[0] - 1, dtype=np.int64), np.diff(ptr))
+    return np.stack([i, np.asarray(j, np.int64), np.asarray(w, np.int64)], 1)
+
+
+@pytest.mark.parametrize("dual", [False, True])
+def test_build_csr_matches_oracle(medium, dual):
+    h, dh = medium
+    for s in (2, 5):
+        want = want_lg(h, s, dual)
+        ptr, j, w = slg.build_csr(dh, s, dual=dual)
+        R = h.n if dual else h.m
+        assert ptr.shape[0] == R + 1 and int(ptr[-1]) == want.shape[0]
+        got = _csr_to_triples(ptr.cpu().numpy(), j.cpu().numpy(), w.cpu().numpy())
+        assert np.array_equal(got, want)
+
+
+def test_build_host_many_both_forms(medium):
+    # one upload, four builds; two in compressed row form, two as triples;
+    # every result equals the oracle's; a query with too small a capacity
+    # reports its count without stopping the others
+    h, _ = medium
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).pin_memory()
+
+    class HostH:
+        pass
+    hh = HostH()
+    hh.m, hh.n = h.m, h.n
+    hh.e_off, hh.e_idx, hh.v_off, hh.v_idx = (pin(h.e_off), pin(h.e_idx), pin(h.v_off),
+                                              pin(h.v_idx))
+    jobs = [(True, 2, True), (False, 2, False), (True, 6, False), (False, 3, True)]
+    wants = [want_lg(h, s, dual) for dual, s, _ in jobs]
+    queries = []
+    for (dual, s, csr), want in zip(jobs, wants):
+        cap = want.shape[0] + 3
+        q = {"s": s, "dual": dual, "capacity": cap,
+             "out_j": torch.full((cap,), -1, dtype=torch.int32).pin_memory(),
+             "out_w": torch.full((cap,), -1, dtype=torch.int32).pin_memory()}
+        if csr:
+            q["row_ptr"] = torch.full(((h.n if dual else h.m) + 1,), -1,
+                                      dtype=torch.int64).pin_memory()
+        else:
+            q["out_i"] = torch.full((cap,), -1, dtype=torch.int32).pin_memory()
+        queries.append(q)
+    small = {"s": 2, "dual": True, "capacity": 5, "out_i": np.zeros(5, np.int32),
+             "out_j": np.zeros(5, np.int32), "out_w": np.zeros(5, np.int32)}
+    res = slg.build_host_many(hh, queries[:2] + [small] + queries[2:])
+    assert [r[0] for r in res] == [0, 0, 2, 0, 0]
+    assert res[2][1] == wants[0].shape[0]
+    for (dual, s, csr), want, q, (st, n) in zip(jobs, wants, queries, res[:2] + res[3:]):
+        assert n == want.shape[0]
+        if csr:
+            got = _csr_to_triples(q["row_ptr"].numpy(), q["out_j"][:n].numpy(),
+                                  q["out_w"][:n].numpy())
+        else:
+            got = np.stack([q["out_i"][:n].numpy(), q["out_j"][:n].numpy(),
+                            q["out_w"][:n].numpy()], 1).astype(np.int64)
+        assert np.array_equal(got, want), (dual, s, csr)
+        assert int(q["out_j"][n]) == -1  # nothing past the pairs
+
+
+def test_build_host_csr_entry_point(medium):
+    h, _ = medium
+    want = want_lg(h, 4, True)
+    R = h.n
+    ptr = np.full(R + 1, -1, np.int64)
+    j = np.zeros(want.shape[0] + 1, np.int32)
+    w = np.zeros(want.shape[0] + 1, np.int32)
+    n = ctypes.c_int64(0)
+    st = slg._host_struct(h)
+    rc = slg.load().slg_build_host_csr(ctypes.byref(st), 4, slg.SLG_DUAL, ptr.ctypes.data,
+                                       j.ctypes.data, w.ctypes.data, j.shape[0],
+                                       ctypes.byref(n), None)
+    assert rc == 0 and n.value == want.shape[0]
+    assert np.array_equal(_csr_to_triples(ptr, j[:n.value], w[:n.value]), want)
+    # relabelling and the SpGEMM path have no row form
+    for flags in (slg.SLG_DUAL | slg.SLG_RELABEL_ASC, slg.SLG_DUAL | slg.SLG_ALGO_SPGEMM):
+        assert slg.load().slg_build_host_csr(ctypes.byref(st), 4, flags, ptr.ctypes.data,
+                                             j.ctypes.data, w.ctypes.data, j.shape[0],
+                                             ctypes.byref(n), None) == 6
