@@ -301,18 +301,6 @@ cudaError_t giant_scratch(Call &c, int32_t max_work, WalkLaunch *L) {
   return e;
 }
 
-// Per-CTA scratch of the sparse bin (staged builds only): the pairs of one
-// row, at most half its wedges, as j then w.
-cudaError_t sparse_scratch(Call &c, int32_t max_work, WalkLaunch *L) {
-  L->sparse_scratch = nullptr;
-  L->sparse_stride = 0;
-  if (max_work <= 0 || L->a.mode != kStage) return cudaSuccess;
-  const long long stride = 2ll * (max_work / 2 + 1);
-  cudaError_t e = c.pool->get(&L->sparse_scratch, (size_t)sparse_ctas() * (size_t)stride);
-  if (e == cudaSuccess) L->sparse_stride = stride;
-  return e;
-}
-
 thread_local int32_t t_err_where = 0;  // kWhere* of the last device-raised error
 
 int read_meta(Call &c) {
@@ -466,16 +454,20 @@ int run_binned(Call &c, int64_t *result) {
   if (rc) return rc;
   // (core rows may have no wedges but still need a giant CTA; their pairs,
   // staged in the same scratch, also come from up to n_core tile items)
-  const int32_t max_giant = c.meta_host->rows_bin[kBinGiant]
-                                ? std::max(c.meta_host->max_giant_work, (int32_t)1) +
-                                      (core.T ? core.n_core : 0)
-                                : 0;
-  const int32_t max_sparse =
-      c.meta_host->rows_bin[kBinSparse] ? std::max(c.meta_host->max_sparse_work, (int32_t)1) : 0;
+  // (a sparse-bin row whose candidates overflow its table is handed to the
+  // giant bin, so the giant scratch also covers the sparse rows)
+  const Meta &mp = *c.meta_host;
+  const int32_t max_giant =
+      (mp.rows_bin[kBinGiant] || mp.rows_bin[kBinSparse])
+          ? std::max(std::max(mp.max_giant_work, mp.max_sparse_work), (int32_t)1) +
+                (core.T ? core.n_core : 0)
+          : 0;
+  // the giant bin's list as planned (the walk may append overflow rows)
+  const unsigned long long giant_rows0 = mp.rows_bin[kBinGiant];
+  const unsigned giant_rest0 = mp.giant_rest;
   WalkLaunch L = walk_launch(c, c.op == kOpBuild ? kStage : kCount, c.smin, c.row_begin);
   L.a.core = core;
   SLG_TRY(giant_scratch(c, max_giant, &L));
-  SLG_TRY(sparse_scratch(c, max_sparse, &L));
   L.w.r_off = c.sd.r_off;
   L.w.r_idx = c.sd.r_idx;
   L.w.c_idx_s = w.c_idx_s;
@@ -507,6 +499,12 @@ int run_binned(Call &c, int64_t *result) {
       // Staging too small: walk again, writing straight to the output.
       SLG_TRY(cudaMemsetAsync(&w.meta->giant_ticket, 0, sizeof(unsigned int), c.st));
       SLG_TRY(cudaMemsetAsync(&w.meta->sparse_ticket, 0, sizeof(unsigned int), c.st));
+      // back to the planned giant list: the sparse bin hands the same rows
+      // over again
+      SLG_TRY(cudaMemcpyAsync(&w.meta->rows_bin[kBinGiant], &giant_rows0, sizeof(giant_rows0),
+                              cudaMemcpyHostToDevice, c.st));
+      SLG_TRY(cudaMemcpyAsync(&w.meta->giant_rest, &giant_rest0, sizeof(giant_rest0),
+                              cudaMemcpyHostToDevice, c.st));
       L.a.mode = kDirect;
       L.a.row_ptr = w.row_ptr;
       L.a.out_i = c.out_i;
@@ -811,7 +809,8 @@ int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin
   if (evs.on) {
     stats.profiled = 1;
     stats.ms_plan = evs.ms(kEvPlan, kEvWalk);
-    for (int b = 0; b < kNumBins; ++b) stats.ms_walk[b] = evs.ms(kEvWalk + b, kEvWalk + b + 1);
+    for (int b = 0; b < kNumBins; ++b)
+      stats.ms_walk[b] = evs.ms(kEvWalk + kWalkEv[b], kEvWalk + kWalkEv[b] + 1);
     stats.ms_scan = evs.ms(kEvWalk + kNumBins, kEvScan);
     if (op == kOpBuild) stats.ms_gather = evs.ms(kEvGather0, kEvGather1);
     if (perm) {
@@ -868,8 +867,6 @@ struct slg_plan {
   slg::Work w = {};
   int32_t *giant = nullptr;
   long long giant_stride = 0;
-  int32_t *sparse = nullptr;
-  long long sparse_stride = 0;
   int32_t *out_i = nullptr, *out_j = nullptr, *out_w = nullptr;
   long long *offsets = nullptr;    // [count + 1]
   int64_t pairs = 0;
@@ -923,8 +920,6 @@ cudaError_t enqueue_plan(slg_plan *p, const Bins &bins, cudaStream_t st, int32_t
   L.R = sd.R;
   L.giant_scratch = p->giant;
   L.giant_stride = p->giant_stride;
-  L.sparse_scratch = p->sparse;
-  L.sparse_stride = p->sparse_stride;
   int32_t n = 0;
   if (sd.R > 0) PLAN_TRY(launch_walk(L, st, &n));
   PLAN_TRY(launch_row_scan(sd.R, w, st));
@@ -1530,8 +1525,6 @@ extern "C" int slg_plan_create(const slg_hypergraph *hs, const int32_t *s, int32
   if (max_work > 0) {
     p->giant_stride = 4ll * max_work;
     SLG_TRY(p->mem.get(&p->giant, (size_t)giant_ctas() * (size_t)p->giant_stride));
-    p->sparse_stride = 2ll * (max_work / 2 + 1);
-    SLG_TRY(p->mem.get(&p->sparse, (size_t)sparse_ctas() * (size_t)p->sparse_stride));
   }
   // 4. autotuner: bin thresholds, timed on this batch
   const Bins cands[] = {Bins{}, Bins{64, 1024, 4096}, Bins{128, 512, 4096}, Bins{128, 1024, 2048},

@@ -19,10 +19,11 @@ namespace slg {
 constexpr int kWarp = 32;
 constexpr int32_t kEmpty = -1;
 
-// Row bins by wedge work (the degree-binned scheduler).  Rows above the CTA
-// bins go to the sparse bin when their far ends are sparse in their id span
-// (fewer than one wedge per kDenseRatio ids) and their threshold is at least
-// 2, else to the giant bin (dense rows, s = 1, dense-core rows).
+// Row bins by wedge work (the degree-binned scheduler).  Rows with s >= 2
+// from Bins::bloom up to Bins::sparse wedges go to the sparse bin, the ones
+// above the CTA bins only when their far ends are sparse in their id span
+// (fewer than one wedge per kDenseRatio ids); the other rows above the CTA
+// bins go to the giant bin (dense rows, s = 1, dense-core rows).
 enum Bin : int {
   kBinWarp = 0, kBinCtaS = 1, kBinCtaL = 2, kBinGiant = 3, kBinSparse = 4, kNumBins = 5
 };
@@ -336,12 +337,18 @@ __device__ __forceinline__ int32_t s_of(const int32_t *row_s, int32_t smin, int3
 // `sparse`: sparse rows above the CTA bins up to this work take the sparse
 // bin (larger ones hold more repeated far ends per window than its table,
 // and the giant bin's partition serves them better); 0 turns the bin off.
+// `bloom`: rows with s >= 2 above this work (and at most `sparse`) take the
+// sparse bin also when they are dense or fit a CTA bin.
 #ifndef SLG_SPARSE_MAX_WORK
 #define SLG_SPARSE_MAX_WORK 16384
+#endif
+#ifndef SLG_BLOOM_MIN_WORK
+#define SLG_BLOOM_MIN_WORK 4096
 #endif
 struct Bins {
   int32_t warp = kWarpMaxWork, ctas = kCtaSMaxWork, ctal = kCtaLMaxWork;
   int32_t sparse = SLG_SPARSE_MAX_WORK;
+  int32_t bloom = SLG_BLOOM_MIN_WORK;
 };
 
 // Dense core for the tensor-core tile path (all null / 0 when unused).
@@ -441,8 +448,6 @@ struct WalkLaunch {
   int32_t rows;             // rows in the range (list stride)
   int32_t *giant_scratch;   // [giant_ctas][4 * max giant work] wedge ends + pairs
   long long giant_stride;   // ints per giant CTA
-  int32_t *sparse_scratch;  // [sparse_ctas][stride] staged pairs (j, w) of a sparse row
-  long long sparse_stride;  // ints per sparse CTA (>= the row's work: pairs <= work / 2)
   int32_t R;                // rows of the side (far ends lie in [0, R))
 };
 
@@ -453,7 +458,9 @@ int sparse_ctas();
 constexpr int32_t kGiantMaxR = 1 << 24;
 
 // ev (optional): kNumBins + 1 events recorded before the first and after
-// every bin kernel.
+// every bin kernel, in launch order (warp, CTA small, CTA large, sparse,
+// giant); bin b runs from ev[kWalkEv[b]] to ev[kWalkEv[b] + 1].
+constexpr int kWalkEv[kNumBins] = {0, 1, 2, 4, 3};
 cudaError_t launch_walk(const WalkLaunch &L, cudaStream_t st, int32_t *launches,
                         cudaEvent_t *ev = nullptr);
 cudaError_t launch_row_scan(int32_t rows, const Work &w, cudaStream_t st);

@@ -261,12 +261,12 @@ __global__ __launch_bounds__(kRowsNT) void k_rows_work(Side s, int32_t smin, int
     if (my_work > 0 || forced) {
       const int32_t e = r0 + threadIdx.x;
       my_bin = forced ? (int)kBinGiant : bin_of(my_work, bins);
-      // a large row up to bins.sparse wedges whose far ends are sparse in
-      // its span (f in (e, R)) and whose threshold is at least 2 takes the
-      // sparse bin
-      if (my_bin == kBinGiant && !forced && my_work <= bins.sparse &&
+      // a row with s >= 2 from bins.bloom up to bins.sparse wedges takes the
+      // sparse bin; above the CTA bins only when its far ends are sparse in
+      // its span (f in (e, R))
+      if (!forced && my_work > bins.bloom && my_work <= bins.sparse &&
           s_of(s.row_s, smin, e) >= 2 &&
-          (long long)my_work * kDenseRatio < (long long)(s.R - 1 - e))
+          (my_bin != kBinGiant || (long long)my_work * kDenseRatio < (long long)(s.R - 1 - e)))
         my_bin = kBinSparse;
       if (my_bin == kBinGiant) atomicMax(&meta->max_giant_work, my_work);
       if (my_bin == kBinSparse) atomicMax(&meta->max_sparse_work, my_work);

@@ -293,10 +293,10 @@ __device__ __forceinline__ int32_t run_below(const unsigned long long *a, unsign
 //  - larger n: a bitonic sort in place over [0, n2), n2 = 2^ceil(log2 n).
 // `*used` receives the end of the region touched; it stays within
 // max(T, 2 n + 32) <= the table's capacity for T >= 2 n.
-template <int NT>
+template <int NT, bool RUNS = (NT >= 512)>
 __device__ __forceinline__ int32_t sort_survivors(unsigned long long *tab, int32_t n,
                                                   int32_t *used) {
-  constexpr bool kRuns = NT >= 512;
+  constexpr bool kRuns = RUNS;
   if (n <= (kRuns ? 64 : 512)) {
     for (int32_t i = threadIdx.x; i < n; i += NT) {
       const unsigned long long x = tab[i];
@@ -309,7 +309,7 @@ __device__ __forceinline__ int32_t sort_survivors(unsigned long long *tab, int32
     return n;
   }
   if constexpr (kRuns) {
-    if (n <= 2 * NT) {
+    if (n <= 8 * NT) {
       const int32_t nr = (n + 31) >> 5;
       for (int32_t r = (int32_t)threadIdx.x >> 5; r < nr; r += NT / 32) {
         const int32_t i = (r << 5) + (int32_t)(threadIdx.x & 31);
@@ -370,10 +370,10 @@ __device__ __forceinline__ int32_t sort_survivors(unsigned long long *tab, int32
 // Returns the number of survivors; with `sort` they are in ascending f at
 // tab[*sorted_at, *sorted_at + count), and tab[0, *used) must be cleared
 // after use (table_reset_front).
-template <int NT, int SPT>
+template <int NT, int SPT, bool RUNS = (NT >= 512)>
 __device__ __forceinline__ int32_t table_collect(unsigned long long *tab, int32_t T, int32_t smin,
                                                  bool sort, int32_t *ws, int32_t *sorted_at,
-                                                 int32_t *used) {
+                                                 int32_t *used, int32_t sort_cap = 0x7fffffff) {
   constexpr int RND = SPT < 8 ? SPT : 8;
   int32_t run = 0;
   for (int32_t r0 = 0; r0 * NT < T; r0 += RND) {
@@ -396,10 +396,11 @@ __device__ __forceinline__ int32_t table_collect(unsigned long long *tab, int32_
     run += total;
   }
   *used = T;
+  if (sort && run > sort_cap) return -1;  // uniform: too many to order in the table
   if (sort && run > 0) {
     __syncthreads();  // compaction writes done
     int32_t u;
-    *sorted_at = sort_survivors<NT>(tab, run, &u);
+    *sorted_at = sort_survivors<NT, RUNS>(tab, run, &u);
     *used = max(T, u);
   }
   return run;
@@ -973,322 +974,271 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
 // Large rows whose far ends are sparse in their id span, with s >= 2.  Almost
 // every far end of such a row occurs once (on the Chung-Lu workloads about
 // 96 % of the wedges of these rows are the only wedge to their far end), and
-// a far end with a single wedge can never reach s >= 2.  So a CTA (one per
-// SM) keeps one bit per id of a window of the span: the first wedge to f sets
-// f's bit (one shared atomicOr) and does nothing else; only a wedge that finds
-// the bit already set -- a repeat -- goes to a small shared hash table, whose
-// count word holds the repeats of f minus one, so |e ∩ f| = count word + 2.
-// When a count reaches s, f's bit in a summary bitmap (one bit per 32 ids)
-// is set.
-//
-// Emission needs no sort: thread t owns 1024 consecutive ids of the window
-// (one summary word, 32 words of the seen bitmap).  It looks up the seen ids
-// of its summary-marked words in the table and counts its pairs; a block scan
-// places every thread's pairs, and a second pass writes them, in ascending f,
-// and clears the thread's own bits.  No survivor list, no single shared
-// counter: the only shared atomics are the per-wedge bit, the repeats and the
-// summary bits.
-//
-// Window: 2^kSpWinLog ids of the span [f_lo, R), processed in ascending
-// order, so the row's output comes out sorted.  If the repeats table of a
-// window gets too full (a probe sequence longer than kSpMaxProbe), the window
-// is given up -- its bits cleared -- and redone at half the width; a window
-// of at most kSpT / 4 ids can never overflow.  The first walk of a row of at
-// most kSpCache wedges keeps every far end in shared memory, so that its
-// later windows read them from there instead of walking again.
+// a far end with a single wedge can never reach s >= 2.  The row is counted
+// in two walks with little shared memory, so that several rows are in
+// flight on each SM (the walk's far-end gathers are latency-bound: a row at
+// a time per SM leaves the memory system idle):
+//   1. every wedge sets its far end's bit in a one-hash Bloom filter (one
+//      shared atomicOr); a wedge that finds the bit already set makes f a
+//      candidate: f is claimed in a small shared table (key, count 0) and
+//      marked in a second filter.  Every f with two or more wedges becomes
+//      a candidate (its second wedge finds the bit set); so may a few
+//      single-wedge f whose bit another f had set;
+//   2. a second walk counts, exactly, every wedge whose far end is a
+//      candidate (the second filter screens out almost all others before
+//      the table is probed).  The count of f is then |e ∩ f|.
+// The candidates with count >= s are sorted and emitted.  A row of at most
+// kSpCache wedges keeps its far ends in shared memory during the first walk
+// and reads them from there in the second.  A row whose candidates overflow
+// the table (a probe sequence longer than kSpMaxProbe) is handed to the
+// giant bin, which runs after this one.
 
 #ifndef SLG_SP_NT
-#define SLG_SP_NT 1024
+#define SLG_SP_NT 256
+#endif
+#ifndef SLG_SP_LOGB
+#define SLG_SP_LOGB 17
 #endif
 #ifndef SLG_SP_LGT
 #define SLG_SP_LGT 12
 #endif
 #ifndef SLG_SP_CACHE
-#define SLG_SP_CACHE 8192
+#define SLG_SP_CACHE 0
 #endif
 #ifndef SLG_SP_MINB
-#define SLG_SP_MINB 1
+#define SLG_SP_MINB 4
 #endif
-constexpr int kSpNT = SLG_SP_NT;
-constexpr int kSpWinLog = 31 - __builtin_clz(kSpNT) + 10;  // 1024 ids per thread
-constexpr int kSpWords = 1 << (kSpWinLog - 5);              // seen bitmap words
-constexpr int kSpCache = SLG_SP_CACHE;                      // far ends kept of a small row
-constexpr int kSpLgT = SLG_SP_LGT;
-constexpr int kSpT = 1 << kSpLgT;                           // repeats table slots
-constexpr int kSpMaxProbe = 48;
 #ifndef SLG_SP_G
 #define SLG_SP_G 6
 #endif
-constexpr int kSpG = SLG_SP_G;                              // wedges per thread per walk step
-static_assert(kSpWords / 32 == kSpNT, "one summary word per thread");
+#ifndef SLG_SP_RUNS
+#define SLG_SP_RUNS 1  // order survivor sets above 64 by sorted warp runs
+#endif
+constexpr int kSpNT = SLG_SP_NT;
+constexpr int kSpLogB = SLG_SP_LOGB;          // Bloom filter bits (log2)
+constexpr int kSpWords = 1 << (kSpLogB - 5);
+constexpr int kSpCWords = kSpWords / 4;       // candidate filter words
+constexpr int kSpLgT = SLG_SP_LGT;
+constexpr int kSpT = 1 << kSpLgT;             // candidate table slots
+constexpr int kSpCache = SLG_SP_CACHE;        // far ends kept of a small row
+constexpr int kSpMaxProbe = 32;
+constexpr int kSpG = SLG_SP_G;                // wedges per thread per walk step
+constexpr int kSpSPT = kSpT / kSpNT;          // table slots per thread
+static_assert(kSpSPT >= 1 && kSpWords % (4 * kSpNT) == 0 && kSpCWords % 4 == 0,
+              "sparse bin geometry");
 
-// [s_base 8][s_flag 4: overflow][s_row 4][pad 16][seen bitmap kSpWords x 4]
-// [table kSpT x 8][summary kSpNT x 4][cache kSpCache x 4][s_beg NT]
-// [s_pref NT+1][ws NT/32+1]
+// [s_base 8][s_ovf 4][s_row 4][pad 16][filter kSpWords x 4]
+// [candidate filter kSpCWords x 4][table kSpT x 8][cache kSpCache x 4]
+// [s_beg NT][s_pref NT+1][ws NT/32+1]
 constexpr size_t sparse_smem() {
-  return 32 + (size_t)kSpWords * 4 + (size_t)kSpT * 8 + (size_t)kSpNT * 4 +
+  return 32 + (size_t)kSpWords * 4 + (size_t)kSpCWords * 4 + (size_t)kSpT * 8 +
          (size_t)kSpCache * 4 + (size_t)(2 * kSpNT + 1 + kSpNT / 32 + 1) * 4;
 }
 
-// A repeat of far end f (its bit was already set).  The first repeat claims
-// f's slot (32-bit CAS on the key word; the count word stays 0: |e ∩ f| = 2),
-// later ones add to the count word.  Unweighted: a pair that reached s is
-// not counted further.  Returns true when this wedge brought |e ∩ f| to s.
-// A probe sequence longer than max_probe marks the window as overflowed
-// (it will be redone); once marked, nothing more is inserted.
-__device__ __forceinline__ bool sparse_repeat(unsigned long long *tab, int32_t f, int32_t smin,
-                                              bool unweighted, int32_t *s_ovf,
-                                              int max_probe) {
-  if (*(volatile int32_t *)s_ovf) return false;
-  uint32_t h = ((uint32_t)f * 0x9E3779B1u) >> (32 - kSpLgT);
-  for (int probe = 0; probe < max_probe; ++probe) {
-    uint32_t *cw = count_word(tab, h);
-    const uint32_t k = atomicCAS(cw + 1, 0xFFFFFFFFu, (uint32_t)f);
-    if (k == 0xFFFFFFFFu) return smin <= 2;  // first repeat: |e ∩ f| = 2
-    if (k == (uint32_t)f) {
-      if (unweighted && (int32_t)*(volatile uint32_t *)cw + 2 >= smin) return false;
-      const int32_t old = (int32_t)atomicAdd(cw, 1u);
-      return old + 2 < smin && old + 3 >= smin;
-    }
-    h = (h + 1) & (kSpT - 1);
-  }
-  *(volatile int32_t *)s_ovf = 1;
-  return false;
+// A row's filter has 2^lgb bits (its candidate filter 2^(lgb - 2)) and its
+// table 2^lgt slots, sized by the row's work (see sp_sizes).
+__device__ __forceinline__ uint32_t sp_h1(int32_t f, int lgb) {  // Bloom filter bit
+  return ((uint32_t)f * 0x9E3779B1u) >> (32 - lgb);
+}
+__device__ __forceinline__ uint32_t sp_h2(int32_t f, int lgb) {  // candidate filter bit
+  return ((uint32_t)f * 0x85EBCA6Bu) >> (34 - lgb);
+}
+__device__ __forceinline__ uint32_t sp_ht(int32_t f, int lgt) {  // candidate table slot
+  return ((uint32_t)f * 0xC2B2AE35u) >> (32 - lgt);
 }
 
-// |e ∩ f| of a seen far end f: 2 + its count word if f repeated, else 1.
-__device__ __forceinline__ int32_t sparse_weight(const unsigned long long *tab, int32_t f) {
-  uint32_t h = ((uint32_t)f * 0x9E3779B1u) >> (32 - kSpLgT);
-  for (int probe = 0; probe < kSpT; ++probe) {
-    const unsigned long long x = tab[h];
-    const uint32_t k = (uint32_t)(x >> 32);
-    if (k == (uint32_t)f) return (int32_t)(uint32_t)x + 2;
-    if (k == 0xFFFFFFFFu) break;
-    h = (h + 1) & (kSpT - 1);
+// Per-row sizes: a filter of >= 32 bits per wedge (so that a single-wedge
+// far end finds its bit set by another with probability below 1/64 on
+// average) and a table of >= one slot per wedge (every candidate has two
+// wedges or is such a collision), within the shared-memory maxima.
+__device__ __forceinline__ void sp_sizes(int32_t work, int *lgb, int *lgt) {
+  const int lw = ceil_log2(work > 1 ? work : 2);
+  *lgb = min(max(lw + 5, 12), kSpLogB);
+  *lgt = min(max(lw, 7), kSpLgT);
+}
+
+// Pass 1: f is a candidate (its filter bit was already set).  Claims f's
+// table slot (32-bit CAS on the key word; the count word stays 0) unless it
+// is there already, and marks it in the candidate filter.  A probe sequence
+// longer than kSpMaxProbe marks the row as overflowed.
+__device__ __forceinline__ void sp_candidate(unsigned long long *tab, uint32_t *cand, int32_t f,
+                                             int32_t *s_ovf, int lgb, int lgt) {
+  if (*(volatile int32_t *)s_ovf) return;
+  const uint32_t mask = (1u << lgt) - 1u;
+  uint32_t h = sp_ht(f, lgt);
+  for (int probe = 0; probe < kSpMaxProbe; ++probe) {
+    const uint32_t k = atomicCAS(count_word(tab, h) + 1, 0xFFFFFFFFu, (uint32_t)f);
+    if (k == 0xFFFFFFFFu) {
+      const uint32_t c = sp_h2(f, lgb);
+      atomicOr(cand + (c >> 5), 1u << (c & 31));
+      return;
+    }
+    if (k == (uint32_t)f) return;
+    h = (h + 1) & mask;
   }
-  return 1;
+  *(volatile int32_t *)s_ovf = 1;
+}
+
+// Pass 2: one wedge to f; counted when f is a candidate.  Unweighted: a
+// count that reached s is not raised further.
+__device__ __forceinline__ void sp_count(unsigned long long *tab, const uint32_t *cand,
+                                         int32_t f, int32_t smin, bool unweighted, int lgb,
+                                         int lgt) {
+  const uint32_t c = sp_h2(f, lgb);
+  if (!(cand[c >> 5] & (1u << (c & 31)))) return;
+  const uint32_t mask = (1u << lgt) - 1u;
+  uint32_t h = sp_ht(f, lgt);
+  for (int probe = 0; probe < kSpMaxProbe; ++probe) {
+    uint32_t *cw = count_word(tab, h);
+    const uint32_t k = cw[1];
+    if (k == (uint32_t)f) {
+      if (!unweighted || (int32_t)*(volatile uint32_t *)cw < smin) atomicAdd(cw, 1u);
+      return;
+    }
+    if (k == 0xFFFFFFFFu) return;
+    h = (h + 1) & mask;
+  }
 }
 
 __global__ __launch_bounds__(kSpNT, SLG_SP_MINB) void k_walk_sparse(
-    Walk w, const int32_t *__restrict__ rows, EmitArgs a, int32_t *__restrict__ scratch,
-    long long scratch_stride, int32_t R, int32_t list_len) {
+    Walk w, const int32_t *__restrict__ rows, EmitArgs a, int32_t *__restrict__ giant_rows,
+    int32_t list_len) {
   Meta *meta = a.meta;
   if (meta->err) return;
   extern __shared__ __align__(16) unsigned char smem[];
   long long *s_base = reinterpret_cast<long long *>(smem);
   int32_t *s_ovf = reinterpret_cast<int32_t *>(smem + 8);
   int32_t *s_row = reinterpret_cast<int32_t *>(smem + 12);
-  uint32_t *bm = reinterpret_cast<uint32_t *>(smem + 32);
-  unsigned long long *tab = reinterpret_cast<unsigned long long *>(bm + kSpWords);
-  uint32_t *summ = reinterpret_cast<uint32_t *>(tab + kSpT);
-  int32_t *cache = reinterpret_cast<int32_t *>(summ + kSpNT);
+  uint32_t *filt = reinterpret_cast<uint32_t *>(smem + 32);
+  uint32_t *cand = filt + kSpWords;
+  unsigned long long *tab = reinterpret_cast<unsigned long long *>(cand + kSpCWords);
+  int32_t *cache = reinterpret_cast<int32_t *>(tab + kSpT);
   int32_t *s_beg = cache + kSpCache;
   int32_t *s_pref = s_beg + kSpNT;
   int32_t *ws = s_pref + kSpNT + 1;
-  // per-CTA global scratch: the pairs of a row spread over several windows,
-  // j then w (<= work / 2 each)
-  const long long half = scratch_stride / 2;
-  int32_t *tj = scratch ? scratch + (long long)blockIdx.x * scratch_stride : nullptr;
-  int32_t *tw = tj ? tj + half : nullptr;
   const int32_t tid = (int32_t)threadIdx.x;
-
-  {
-    uint4 *b4 = reinterpret_cast<uint4 *>(bm);
-    for (int i = tid; i < kSpWords / 4; i += kSpNT) b4[i] = make_uint4(0, 0, 0, 0);
-  }
-  summ[tid] = 0u;
+  // clears the first 2^(lgb - 5) filter words and 2^(lgb - 7) candidate
+  // filter words (>= 128 and 32: whole uint4 groups)
+  auto clear_filters = [&](int lgb) {
+    uint4 *f4 = reinterpret_cast<uint4 *>(filt);
+    for (int i = tid; i < (1 << (lgb - 7)); i += kSpNT) f4[i] = make_uint4(0, 0, 0, 0);
+    uint4 *c4 = reinterpret_cast<uint4 *>(cand);
+    for (int i = tid; i < (1 << (lgb - 9)); i += kSpNT) c4[i] = make_uint4(0, 0, 0, 0);
+  };
+  clear_filters(kSpLogB);
+  for (int i = tid; i < kSpT; i += kSpNT) tab[i] = kEmpty64;
   const unsigned nrows = (unsigned)meta->rows_bin[kBinSparse];
   const unsigned nhuge = meta->sparse_huge;
-  auto row_of = [&](unsigned t) -> int32_t {
-    return t >= nrows ? -1 : rows[t < nhuge ? t : list_len - 1 - (t - nhuge)];
-  };
-  // rows above kGiantHugeWork first; the next row's ticket is taken while a
-  // row is processed
-  if (tid == 0) *s_row = row_of(atomicAdd(&meta->sparse_ticket, 1u));
   const bool unweighted = a.unweighted != 0;
-  // SM cycles of the CTA's first thread: row set-up, walk, count and place,
-  // write and clear, row end
+  const bool emit = a.mode != kCount;
+  // SM cycles of the CTA's first thread: row set-up, first walk, second
+  // walk, collect and order, emit and clear
   long long cyc[5] = {0, 0, 0, 0, 0};
   for (;;) {
     long long t0 = clock64();
-    __syncthreads();  // s_row set; the previous row's bits, summary and scratch copy done
+    __syncthreads();  // the previous row's clears done
+    if (tid == 0) {
+      const unsigned t = atomicAdd(&meta->sparse_ticket, 1u);
+      *s_ovf = 0;
+      *s_row = t >= nrows ? -1 : rows[t < nhuge ? t : list_len - 1 - (t - nhuge)];
+    }
+    __syncthreads();
     const int32_t e = *s_row;
     if (e < 0) break;
-    unsigned t_next = 0;
-    if (tid == 0) t_next = atomicAdd(&meta->sparse_ticket, 1u);  // used at the row's end
     const int32_t smin = s_of(a.row_s, a.smin, e);
-    const int32_t f_lo = a.full_rows ? 0 : e + 1;
     const int32_t work = a.row_work[e - a.row_begin];
     const int32_t k0 = w.r_off[e], k1 = w.r_off[e + 1];
     const bool cached = work <= kSpCache;
-    if (a.mode == kStage && (long long)work / 2 > half) {  // scratch sized by the largest row
-      if (tid == 0) raise_error(meta, SLG_ERR_INVALID, kWhereGiant);
-      break;
-    }
-    long long base = a.mode == kDirect ? a.row_ptr[e - a.row_begin] : -1;
-    int32_t out = 0;             // pairs of the row so far
-    bool placed = false;         // STAGE: the row's pairs went straight to the staging area
-    bool failed = false;
-    int32_t width = 1 << kSpWinLog;
-    bool first = true;
+    int lgb, lgt;
+    sp_sizes(work, &lgb, &lgt);
+    const int32_t T = 1 << lgt;
     {
       const long long t1 = clock64();
       cyc[0] += t1 - t0;
       t0 = t1;
     }
-    for (int32_t wlo = f_lo; wlo < R;) {
-      const int32_t whi = (R - wlo > width) ? wlo + width : R;
-      const int max_probe = width <= kSpT / 4 ? kSpT : kSpMaxProbe;
-      __syncthreads();  // the previous window's look-ups done
-      {
-        ulonglong2 *t2 = reinterpret_cast<ulonglong2 *>(tab);
-        const ulonglong2 em = make_ulonglong2(kEmpty64, kEmpty64);
-        for (int i = tid; i < kSpT / 2; i += kSpNT) t2[i] = em;
-        if (tid == 0) *s_ovf = 0;
-      }
-      auto visit = [&](int32_t f, uint32_t bo, uint32_t mo) {
-        if ((bo & mo) && sparse_repeat(tab, f, smin, unweighted, s_ovf, max_probe)) {
-          const uint32_t b = (uint32_t)(f - wlo);
-          atomicOr(summ + (b >> 10), 1u << ((b >> 5) & 31));
-        }
-      };
-      if (first || !cached) {
-        const bool keep = first && cached;
-        // (the walk's scan barriers order the table clear before any insert)
-        // every bit of a step is set before any result is looked at, so a
-        // thread's G shared atomics are in flight together
-        cta_walk_batched<kSpNT, kSpG>(
-            w, k0, k1, s_beg, s_pref, ws, [&](const int32_t(&f)[kSpG], int32_t i0) {
-              uint32_t old[kSpG], m[kSpG];
+    // 1. filter; candidates (a thread's G filter updates are in flight together)
+    cta_walk_batched<kSpNT, kSpG>(
+        w, k0, k1, s_beg, s_pref, ws, [&](const int32_t(&f)[kSpG], int32_t i0) {
+          uint32_t old[kSpG], m[kSpG];
 #pragma unroll
-              for (int g = 0; g < kSpG; ++g) {
-                if (keep && f[g] >= 0) cache[i0 + 32 * g] = f[g];
-                const bool in = f[g] >= wlo && f[g] < whi;  // f < 0: no wedge
-                const uint32_t b = (uint32_t)(f[g] - wlo);
-                m[g] = in ? 1u << (b & 31) : 0u;
-                old[g] = in ? atomicOr(bm + (b >> 5), m[g]) : 0u;
-              }
-#pragma unroll
-              for (int g = 0; g < kSpG; ++g) visit(f[g], old[g], m[g]);
-            });
-      } else {
-        __syncthreads();  // table clear before the inserts
-        for (int32_t i = tid; i < work; i += kSpNT) {
-          const int32_t f = cache[i];
-          if (f >= wlo && f < whi) {
-            const uint32_t b = (uint32_t)(f - wlo), m = 1u << (b & 31);
-            visit(f, atomicOr(bm + (b >> 5), m), m);
+          for (int g = 0; g < kSpG; ++g) {
+            if (cached && f[g] >= 0) cache[i0 + 32 * g] = f[g];
+            const uint32_t h = sp_h1(f[g], lgb);
+            m[g] = f[g] >= 0 ? 1u << (h & 31) : 0u;
+            old[g] = f[g] >= 0 ? atomicOr(filt + (h >> 5), m[g]) : 0u;
           }
-        }
-      }
-      first = false;
-      __syncthreads();  // every insert done
-      {
-        const long long t1 = clock64();
-        cyc[1] += t1 - t0;
-        t0 = t1;
-      }
-      // thread t's ids: [wlo + 1024 t, + 1024); its seen words [32 t, 32 t + 32)
-      const int32_t nw = (int32_t)(((uint32_t)(whi - wlo) + 31u) >> 5);  // words in use
-      const int32_t w0 = tid * 32;
-      auto clear_own = [&]() {
-        if (w0 < nw) {
-          uint4 *b4 = reinterpret_cast<uint4 *>(bm + w0);
 #pragma unroll
-          for (int q = 0; q < 8; ++q) b4[q] = make_uint4(0, 0, 0, 0);
-          summ[tid] = 0u;
-        }
-      };
-      if (*s_ovf) {  // uniform: read after the barrier
-        clear_own();
-        if (width <= kSpT / 4) {  // cannot overflow: a bound was broken
-          if (tid == 0) raise_error(meta, SLG_ERR_INVALID, kWhereHash);
-          failed = true;
-          break;
-        }
-        width >>= 1;  // retry the same ids, narrower
-        continue;
-      }
-      // pass 1: this thread's pairs
-      const uint32_t sw = w0 < nw ? summ[tid] : 0u;
-      int32_t c = 0;
-      for (uint32_t q = sw; q; q &= q - 1) {
-        const int32_t wi = w0 + __ffs(q) - 1;
-        for (uint32_t x = bm[wi]; x; x &= x - 1) {
-          const int32_t f = wlo + wi * 32 + __ffs(x) - 1;
-          c += sparse_weight(tab, f) >= smin;
-        }
-      }
-      int32_t n;
-      const int32_t inc = block_inclusive_scan<kSpNT>(c, ws, &n);
-      // where the window's pairs go: the row's own place in the staging area
-      // when this window holds all of them, else the CTA's scratch
-      const bool to_stage = a.mode == kStage && out == 0 && whi == R;
-      if (to_stage) {
-        if (tid == 0) *s_base = reserve(a, e, n, kBinSparse);
-        __syncthreads();
-        base = *s_base;
-        placed = true;
-      }
-      if (a.mode == kStage && !to_stage && out + n > half) {
-        if (tid == 0) raise_error(meta, SLG_ERR_INVALID, kWhereGiant);
-        clear_own();
-        failed = true;
-        break;
-      }
-      {
-        const long long t1 = clock64();
-        cyc[2] += t1 - t0;
-        t0 = t1;
-      }
-      // pass 2: write this thread's pairs in ascending f; clear its bits
-      if (c > 0 && a.mode != kCount) {
-        int32_t p = out + inc - c;
-        for (uint32_t q = sw; q; q &= q - 1) {
-          const int32_t wi = w0 + __ffs(q) - 1;
-          for (uint32_t x = bm[wi]; x; x &= x - 1) {
-            const int32_t f = wlo + wi * 32 + __ffs(x) - 1;
-            const int32_t wt = sparse_weight(tab, f);
-            if (wt < smin) continue;
-            if (a.mode == kDirect) {
-              put(a, base, p, e, f, wt);
-            } else if (to_stage) {
-              if (base >= 0) {
-                a.stage_j[base + p] = f;
-                if (!unweighted) a.stage_w[base + p] = wt;
-              }
-            } else {
-              tj[p] = f;
-              if (!unweighted) tw[p] = wt;
-            }
-            ++p;
-          }
-        }
-      }
-      clear_own();
-      out += n;
-      {
-        const long long t1 = clock64();
-        cyc[3] += t1 - t0;
-        t0 = t1;
-      }
-      wlo = whi;
-      if (width < (1 << kSpWinLog)) width <<= 1;
+          for (int g = 0; g < kSpG; ++g)
+            if (old[g] & m[g]) sp_candidate(tab, cand, f[g], s_ovf, lgb, lgt);
+        });
+    __syncthreads();  // candidates final
+    {
+      const long long t1 = clock64();
+      cyc[1] += t1 - t0;
+      t0 = t1;
     }
-    if (failed) break;
-    if (!placed) {
-      if (tid == 0) *s_base = reserve(a, e, out, kBinSparse);
+    if (*s_ovf) {  // uniform: too many candidates for the table
+      if (tid == 0) {
+        // hand the row to the giant bin (launched after this kernel)
+        const unsigned pos = atomicAdd(&meta->giant_rest, 1u);
+        giant_rows[list_len - 1 - pos] = e;
+        atomicAdd(&meta->rows_bin[kBinGiant], 1ull);
+      }
+      clear_filters(lgb);
+      for (int i = tid; i < T; i += kSpNT) tab[i] = kEmpty64;
+      continue;
+    }
+    // 2. exact counts of the candidates
+    if (cached) {
+      for (int32_t i = tid; i < work; i += kSpNT)
+        sp_count(tab, cand, cache[i], smin, unweighted, lgb, lgt);
+    } else {
+      cta_walk_batched<kSpNT, kSpG>(
+          w, k0, k1, s_beg, s_pref, ws, [&](const int32_t(&f)[kSpG], int32_t) {
+#pragma unroll
+            for (int g = 0; g < kSpG; ++g)
+              if (f[g] >= 0) sp_count(tab, cand, f[g], smin, unweighted, lgb, lgt);
+          });
+    }
+    __syncthreads();  // counts final
+    {
+      const long long t1 = clock64();
+      cyc[2] += t1 - t0;
+      t0 = t1;
+    }
+    // 3. candidates with count >= s, in ascending f at tab[at, at + n)
+    int32_t at = 0, used = T;
+    // (ordering n survivors needs 2 n + 32 slots of the table)
+    const int32_t n = table_collect<kSpNT, kSpSPT, (SLG_SP_RUNS != 0)>(
+        tab, T, smin, emit, ws, &at, &used, (T - 32) / 2);
+    if (n < 0) {  // uniform: hand the row to the giant bin, as for an overflow
       __syncthreads();
-      if (a.mode == kStage) {
-        const long long b = *s_base;
-        if (b >= 0)
-          for (int32_t i = tid; i < out; i += kSpNT) {
-            a.stage_j[b + i] = tj[i];
-            if (!unweighted) a.stage_w[b + i] = tw[i];
-          }
+      if (tid == 0) {
+        const unsigned pos = atomicAdd(&meta->giant_rest, 1u);
+        giant_rows[list_len - 1 - pos] = e;
+        atomicAdd(&meta->rows_bin[kBinGiant], 1ull);
       }
+      clear_filters(lgb);
+      for (int i = tid; i < T; i += kSpNT) tab[i] = kEmpty64;
+      continue;
     }
-    if (tid == 0) *s_row = row_of(t_next);
+    if (tid == 0) *s_base = reserve(a, e, n, kBinSparse);
+    __syncthreads();
+    {
+      const long long t1 = clock64();
+      cyc[3] += t1 - t0;
+      t0 = t1;
+    }
+    const long long base = *s_base;
+    if (emit && base >= 0)
+      for (int32_t i = tid; i < n; i += kSpNT) {
+        const unsigned long long x = tab[at + i];
+        const int32_t f = (int32_t)(x >> 32), c = (int32_t)(uint32_t)x;
+        put(a, base, i, e, f, c);
+      }
+    clear_filters(lgb);  // nothing reads the filters after the second walk
+    table_reset_front<kSpNT>(tab, used);
     cyc[4] += clock64() - t0;
   }
   if (tid == 0)
@@ -1371,15 +1321,17 @@ cudaError_t launch_walk(const WalkLaunch &L, cudaStream_t st, int32_t *launches,
       L.w, lists + 2 * stride, L.row_work, L.a);
   ++n;
   if (ev) cudaEventRecord(ev[3], st);
+  // the sparse bin before the giant bin: a sparse row whose candidates
+  // overflow its table is appended to the giant bin's list
+  k_walk_sparse<<<o.sms * o.sp_blocks, kSpNT, sparse_smem(), st>>>(
+      L.w, lists + 4 * stride, L.a, const_cast<int32_t *>(lists) + 3 * stride, (int32_t)stride);
+  ++n;
+  if (ev) cudaEventRecord(ev[4], st);
   if (L.giant_scratch) {
     k_walk_giant<<<o.sms * o.g_blocks, kGiantNT, giant_smem(), st>>>(
         L.w, lists + 3 * stride, L.a, L.giant_scratch, L.giant_stride, L.R, (int32_t)stride);
     ++n;
   }
-  if (ev) cudaEventRecord(ev[4], st);
-  k_walk_sparse<<<o.sms * o.sp_blocks, kSpNT, sparse_smem(), st>>>(
-      L.w, lists + 4 * stride, L.a, L.sparse_scratch, L.sparse_stride, L.R, (int32_t)stride);
-  ++n;
   if (ev) cudaEventRecord(ev[5], st);
   if (launches) *launches += n;
   return cudaGetLastError();
