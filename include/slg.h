@@ -246,6 +246,19 @@ int slg_build_host_csr(const slg_hypergraph *h, int32_t s, uint32_t flags,
                        int64_t capacity, int64_t *n_pairs, void *stream);
 
 /*
+ * slg_row_work -- the wedge work of every row of the side: work[e] = number
+ * of upper-triangle wedges e -> v -> f (|e|, |f| >= s) the walk visits for
+ * row e (0 for rows of size < s); their sum is W_s (returned in *wedges).
+ * Per-row work is what balances a split of the rows into contiguous ranges
+ * for several GPUs (the parallel loop over hyperedges of Section IV-F).
+ *   work    DEVICE int32 array of R entries (R = rows of the side)
+ *   flags   SLG_DUAL, SLG_NO_PRUNE; binned algorithm only, no relabelling
+ * Synchronises `stream`.  Errors as for slg_count.
+ */
+int slg_row_work(const slg_hypergraph *h, int32_t s, uint32_t flags,
+                 int32_t *work, int64_t *wedges, void *stream);
+
+/*
  * slg_wedges -- W_s, the number of upper-triangle wedges e -> v -> f
  * (f > e, |e| >= s, |f| >= s) that the walk visits: the exact work of the
  * s-overlap step after degree-based pruning (Section IV-C), equal to

@@ -121,6 +121,7 @@ ABI_FUNCTIONS = {
                                           _VP, ctypes.c_int64, _I64P, _VP]),
     "slg_build_host_many": (ctypes.c_int, [_HP, ctypes.POINTER(_Query), ctypes.c_int32,
                                            _VP]),
+    "slg_row_work": (ctypes.c_int, [_HP, ctypes.c_int32, ctypes.c_uint32, _VP, _I64P, _VP]),
     "slg_wedges": (ctypes.c_int, [_HP, ctypes.c_int32, ctypes.c_uint32, _I64P, _VP]),
     "slg_row_offsets": (ctypes.c_int, [_HP, ctypes.c_int32, ctypes.c_uint32, _VP, _VP]),
     "slg_last_stats": (ctypes.c_int, [ctypes.POINTER(_Stats)]),
@@ -455,6 +456,20 @@ def build_stream(h: DeviceHypergraph, s: int, max_pairs: int, dual=False, unweig
         p = int(n.value)
         yield a, b, out[0][:p], out[1][:p], (out[2][:p] if out[2] is not None else None)
         a = b
+
+
+def row_work(h: DeviceHypergraph, s: int, dual=False, stream=None, prune=True):
+    """int32 CUDA tensor [R]: the wedge work of every row (slg_row_work)."""
+    import torch
+    R = h.rows(dual)
+    work = torch.empty(max(R, 1), dtype=torch.int32, device=h.e_off.device)
+    n = ctypes.c_int64(0)
+    rc = load().slg_row_work(ctypes.byref(h.struct), int(s),
+                             _flags(dual, False, "binned", False, None, prune),
+                             work.data_ptr(), ctypes.byref(n), _stream(stream))
+    if rc != 0:
+        raise SlgError(rc, "slg_row_work")
+    return work[:R]
 
 
 def wedges(h: DeviceHypergraph, s: int, dual=False, stream=None) -> int:

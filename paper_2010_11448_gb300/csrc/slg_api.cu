@@ -247,6 +247,7 @@ struct Call {
   int32_t R_pad;
   Op op;
   int32_t *out_i, *out_j, *out_w;
+  int32_t *row_work_out;  // slg_row_work: per-row wedge work (device)
   int64_t capacity;
   cudaStream_t st;
   DeviceCtx *ctx;
@@ -437,6 +438,9 @@ int run_binned(Call &c, int64_t *result) {
   SLG_TRY(launch_rows_work(c.sd, s_prune, c.row_begin, c.row_end, w, core, t_bins, c.st));
   c.launches += 4 + (c.rows > 0 ? 1 : 0);
   if (c.op == kOpWedges) {
+    if (c.row_work_out)
+      SLG_TRY(cudaMemcpyAsync(c.row_work_out, w.row_work, sizeof(int32_t) * (size_t)c.rows,
+                              cudaMemcpyDeviceToDevice, c.st));
     int rc = read_meta(c);
     if (rc) return rc;
     *result = (int64_t)c.meta_host->wedges;
@@ -664,7 +668,8 @@ int run_spgemm(Call &c, int64_t *result) {
 int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin,
         int32_t row_end, Op op, int32_t *out_i, int32_t *out_j, int32_t *out_w,
         int64_t capacity, int64_t *result, cudaStream_t st, const int32_t *row_s = nullptr,
-        int32_t *max_row_work = nullptr, long long *row_ptr_out = nullptr) {
+        int32_t *max_row_work = nullptr, long long *row_ptr_out = nullptr,
+        int32_t *row_work_out = nullptr) {
   int rc = check_args(h, smin, flags);
   if (rc != SLG_OK) return rc;
   if (!result) return SLG_ERR_INVALID;
@@ -695,6 +700,7 @@ int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin
   c.out_w = out_w;
   c.capacity = capacity;
   c.st = st;
+  c.row_work_out = row_work_out;
   const int64_t nnz = c.sd.nnz;
   c.R_pad = (int32_t)(((int64_t)c.sd.R + 1023) / 1024 * 1024);
   if (c.R_pad == 0) c.R_pad = 1024;
@@ -966,7 +972,7 @@ int upload(const slg_hypergraph *hh, Pool &pool, cudaStream_t st, slg_hypergraph
 // once the build is done (the device buffers are released on `cs` after
 // them).  Returns the query's status.
 int host_query(const slg_hypergraph *d, slg_query *q, cudaStream_t st, cudaStream_t cs,
-               cudaEvent_t done) {
+               cudaEvent_t done, std::vector<void *> *keep) {
   q->n_pairs = 0;
   const uint32_t flags = q->flags;
   if (flags & SLG_ASYNC) return SLG_ERR_INVALID;
@@ -1032,7 +1038,10 @@ int host_query(const slg_hypergraph *d, slg_query *q, cudaStream_t st, cudaStrea
     if (c == cudaSuccess && !unweighted)
       c = cudaMemcpyAsync(q->out_w, buf[2], p * 4, cudaMemcpyDeviceToHost, cs);
   }
-  release(cs);
+  // the buffers stay until every copy of the call is done and are then
+  // released on `st`, so that the pool hands them to the next call on `st`
+  for (void *b : buf)
+    if (b) keep->push_back(b);
   if (c != cudaSuccess) {
     cudaGetLastError();
     return SLG_ERR_CUDA;
@@ -1081,6 +1090,16 @@ int slg_row_offsets(const slg_hypergraph *h, int32_t s, uint32_t flags, int64_t 
   int64_t pairs = 0;
   return run(h, s, flags, 0, R, kOpCount, nullptr, nullptr, nullptr, 0, &pairs,
              (cudaStream_t)stream, nullptr, nullptr, reinterpret_cast<long long *>(row_ptr));
+}
+
+int slg_row_work(const slg_hypergraph *h, int32_t s, uint32_t flags, int32_t *work,
+                 int64_t *wedges, void *stream) {
+  if (!h || !work || !wedges) return SLG_ERR_INVALID;
+  if ((flags & SLG_ALGO_MASK) != SLG_ALGO_BINNED || (flags & (SLG_RELABEL_ASC | SLG_RELABEL_DESC)))
+    return SLG_ERR_UNSUPPORTED;
+  const int32_t R = (flags & SLG_DUAL) ? h->n_vertices : h->n_edges;
+  return run(h, s, flags, 0, R, kOpWedges, nullptr, nullptr, nullptr, 0, wedges,
+             (cudaStream_t)stream, nullptr, nullptr, nullptr, work);
 }
 
 int slg_wedges(const slg_hypergraph *h, int32_t s, uint32_t flags, int64_t *wedges,
@@ -1162,16 +1181,20 @@ int slg_build_host_many(const slg_hypergraph *hh, slg_query *queries, int32_t co
     return SLG_ERR_CUDA;
   }
   int first = SLG_OK;
+  std::vector<void *> keep;
   for (int32_t k = 0; k < count; ++k) {
-    const int q = host_query(&d, &queries[k], st, cs, done);
+    const int q = host_query(&d, &queries[k], st, cs, done, &keep);
     queries[k].status = q;
     if (q != SLG_OK && first == SLG_OK) first = q;
   }
-  // every copy back done; the uploaded input is released on `st` (Pool)
-  const cudaError_t e1 = cudaStreamSynchronize(cs);
+  // every copy back done, then the device outputs and the uploaded input
+  // (Pool) are released on `st`
+  cudaError_t e1 = cudaEventRecord(done, cs);
+  if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(st, done, 0);
+  for (void *b : keep) cudaFreeAsync(b, st);
+  const cudaError_t e2 = cudaStreamSynchronize(st);
   cudaEventDestroy(done);
   cudaStreamDestroy(cs);
-  const cudaError_t e2 = cudaStreamSynchronize(st);
   if (e1 != cudaSuccess || e2 != cudaSuccess) {
     cudaGetLastError();
     return SLG_ERR_CUDA;
