@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the plain-kernel and SpGEMM comparison builds")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the dense-core (tiled) and batched comparisons")
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (testing)")
     ap.add_argument("--builds", default="all",
                     help="comma list of builds to run, e.g. 'H:8,H*:2' (profiling)")
@@ -541,6 +543,19 @@ def run_ours(args):
             os.sched_setaffinity(0, saved_affinity)
         del qs, hh
 
+    # the metric's batched and tiled arms (untimed by the step clock; each
+    # compared with its sequential / walk-only counterpart on this GPU)
+    if not args.no_extras:
+        del outs
+        torch.cuda.empty_cache()
+        result["tiled"] = core_comparison(torch, slg, 1.0, (2, 8))
+        result["tiled"]["workload"] = ("web-shaped hypergraph |E|=4M, |V|=10M, lognormal(2,1.5) "
+                                       "sizes capped 1e5, planted core 4096 x 8192 at 0.3")
+        result["tile_kernel"] = tile_roofline(torch, slg)
+        result["batched"] = batch_comparison(torch, slg, 512, 200_000, 5, 2)
+        result["batched"]["workload"] = ("512 Chung-Lu hypergraphs, |E| log-uniform 1k-200k, "
+                                         "|V| = 2|E|, own s ~ U{2..32}; one captured launch")
+
     if rank == 0 and not args.no_cpu:
         oracle.build()
         rate, times, cores, w_full, sample = cpu_oracle_full(h, CPU_FULL_REPS)
@@ -570,83 +585,72 @@ def _setup_gpu():
     return torch, slg
 
 
-def run_batch(args):
-    """Batched form: `batch_count` Chung-Lu hypergraphs (m log-uniform in
-    [1e3, batch_max], n = 2m), each with its own s ~ U{2..32}: captured
-    pipelines (one graph replay per plan of at most 2^24 rows) vs the same
-    builds one call at a time (binned, and the plain per-hyperedge kernel)."""
-    import numpy as np
-    torch, slg = _setup_gpu()
+def batch_comparison(torch, slg, count: int, max_m: int, steps: int, warmup: int):
+    """Batched form: `count` Chung-Lu hypergraphs (m log-uniform in
+    [1e3, max_m], n = 2m), each with its own s ~ U{2..32}, built by one
+    captured pipeline (one CUDA-graph launch for the whole union) vs the same
+    builds one call at a time (binned, and the plain per-hyperedge kernel);
+    the batched lists equal the sequential ones member by member."""
     import hypergen
     t0 = time.perf_counter()
-    members = hypergen.batch(args.batch_count, seed=100, m_lo=1000, m_hi=args.batch_max,
+    members = hypergen.batch(count, seed=100, m_lo=1000, m_hi=max_m,
                              workers=min(16, os.cpu_count() or 1))
-    print(f"batch: generated in {time.perf_counter() - t0:.0f} s", file=sys.stderr, flush=True)
     gen_s = time.perf_counter() - t0
     dhs = [slg.to_device(h) for h, _ in members]
     ss = [s for _, s in members]
     W = sum(slg.wedges(d, s) for d, s in zip(dhs, ss))
-    # one plan per group of members whose union stays within the library's
-    # largest side (2^24 rows); each plan is one captured graph launch
-    groups, cur, rows = [], [], 0
-    for k, d in enumerate(dhs):
-        if cur and rows + d.m > (1 << 24):
-            groups.append(cur)
-            cur, rows = [], 0
-        cur.append(k)
-        rows += d.m
-    groups.append(cur)
     t0 = time.perf_counter()
-    plans = [slg.Plan([dhs[k] for k in g], [ss[k] for k in g]) for g in groups]
+    plan = slg.Plan(dhs, ss)
     plan_s = time.perf_counter() - t0
-    print(f"batch: {len(plans)} plans in {plan_s:.0f} s", file=sys.stderr, flush=True)
-    infos = [p.info() for p in plans]
+    info = plan.info()
     st = torch.cuda.current_stream()
-    for _ in range(args.warmup):
-        for p in plans:
-            p.execute()
+    for _ in range(max(warmup, 1)):
+        plan.execute()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
-    for _ in range(args.steps):
-        for p in plans:
-            p.execute()
+    for _ in range(steps):
+        plan.execute()
     e1.record(st)
     torch.cuda.synchronize()
-    batched_ms = e0.elapsed_time(e1) / args.steps
-    res = [r for p in plans for r in p.results()]
+    batched_ms = e0.elapsed_time(e1) / steps
+    res = plan.results()
     pairs = sum(int(r[0].shape[0]) for r in res)
-    # sequential builds, binned and plain (each call sizes its own output)
     caps = [slg.count(d, s) for d, s in zip(dhs, ss)]
     outs = [slg.alloc_outputs(c) for c in caps]
     seq = {}
     for algo in ("binned", "plain"):
-        for d, s, o in zip(dhs, ss, outs):        # warm
-            slg.build(d, s, algo=algo, out=o)
-            break
+        slg.build(dhs[0], ss[0], algo=algo, out=outs[0])  # warm
         torch.cuda.synchronize()
         t = time.perf_counter()
         for d, s, o in zip(dhs, ss, outs):
             slg.build(d, s, algo=algo, out=o)
         torch.cuda.synchronize()
         seq[algo] = (time.perf_counter() - t) * 1e3
-        print(f"batch: sequential {algo} {seq[algo]:.0f} ms", file=sys.stderr, flush=True)
-    # the batched result equals the sequential one, member by member
     same = all(torch.equal(r[1], o[1][:c]) and torch.equal(r[2], o[2][:c])
                for r, o, c in zip(res, outs, caps))
-    out = {"mode": "batch", "metric": "batched L_s build: one captured launch vs sequential",
-           "members": len(dhs), "incidences": int(sum(d.nnz for d in dhs)),
-           "wedges": int(W), "pairs": pairs, "batched_ms": batched_ms,
-           "batched_wedges_per_s": W / (batched_ms / 1e3),
+    out = {"members": len(dhs), "incidences": int(sum(d.nnz for d in dhs)),
+           "union_rows": int(sum(d.m for d in dhs)), "wedges": int(W), "pairs": pairs,
+           "batched_ms": batched_ms, "batched_wedges_per_s": W / (batched_ms / 1e3),
            "sequential_binned_ms": seq["binned"], "sequential_plain_ms": seq["plain"],
            "speedup_vs_plain": seq["plain"] / batched_ms,
            "speedup_vs_sequential_binned": seq["binned"] / batched_ms,
-           "bit_identical_to_sequential": bool(same), "plans": len(plans),
-           "members_per_plan": [len(g) for g in groups],
-           "autotuned_bins": [i["bins"] for i in infos],
-           "kernels_per_launch": [i["launches"] for i in infos], "plan_s": plan_s,
-           "generate_s": gen_s,
-           "steps": args.steps, "warmup": args.warmup}
+           "bit_identical_to_sequential": bool(same), "plans": 1,
+           "autotuned": dict(zip(["warp", "cta_small", "cta_large", "sparse_max", "sparse_min",
+                                  "dense_ratio"], info["bins"])),
+           "kernels_per_launch": info["launches"], "plan_s": plan_s, "generate_s": gen_s,
+           "steps": steps}
+    del plan, res, outs, dhs
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batch(args):
+    """--mode batch: the batched-form comparison alone."""
+    torch, slg = _setup_gpu()
+    out = {"mode": "batch", "metric": "batched L_s build: one captured launch vs sequential"}
+    out.update(batch_comparison(torch, slg, args.batch_count, args.batch_max, args.steps,
+                                args.warmup))
     print(json.dumps(out), flush=True)
     return 0
 
@@ -708,33 +712,100 @@ def run_serve(args):
     return 0
 
 
-def run_core(args):
-    """Dense core: the lognormal web-shaped hypergraph with a planted core of
-    4096 hyperedges x 8192 vertices at density 0.3; builds at s = 2, 8, 32 on
-    H and H*, with and without the tensor-core tile path (same output)."""
-    torch, slg = _setup_gpu()
+def fp8_peak_tflops(torch):
+    """Dense FP8 (e4m3) tensor throughput of this GPU, measured with
+    torch._scaled_mm (cuBLASLt) on 8192^3, best of 10 (burst).  Falls back to
+    twice the measured bf16 peak (the nominal FP8 / BF16 ratio)."""
+    try:
+        M = N = K = 8192
+        a = torch.randn(M, K, device="cuda").to(torch.float8_e4m3fn)
+        b = torch.randn(N, K, device="cuda").to(torch.float8_e4m3fn).t()
+        one = torch.ones((), device="cuda")
+
+        def f():
+            return torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+        for _ in range(3):
+            f()
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            f()
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        del a, b
+        return 2.0 * M * N * K / (best / 1e3) / 1e12, \
+            "measured: torch._scaled_mm fp8 e4m3 8192^3 (cuBLASLt), best of 10"
+    except Exception as exc:  # noqa: BLE001
+        p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        bf16 = json.load(open(p))["bf16_tflops"] if os.path.exists(p) else 1900.0
+        return 2.0 * bf16, f"bf16 peak x 2 (nominal fp8/bf16); _scaled_mm failed: {exc}"
+
+
+def tile_roofline(torch, slg, rows: int = 4096, cols: int = 8192, density: float = 0.3):
+    """The tensor-core tile kernel alone on the planted core's shape (rows x
+    cols 0/1 at `density`, FP8 0x38 = 1): CUDA-event ms (best of 5), FLOP/s of
+    the upper-triangle tiles it computes, against the FP8 peak; the counts
+    are checked against an FP32 product (exact below 2^24)."""
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    A01 = (torch.rand(rows, cols, device="cuda", generator=g) < density)
+    A = A01.to(torch.uint8) * 0x38
+    slg.set_profiling(True)
+    best = 1e30
+    C = None
+    for _ in range(6):
+        C = slg.tile_overlap(A)
+        best = min(best, slg.last_stats()["ms_tile"])
+    slg.set_profiling(False)
+    nt = rows // 128
+    tasks = nt * (nt + 1) // 2
+    flops = 2.0 * 128 * 128 * cols * tasks
+    ref = (A01.float() @ A01.float().t()).to(torch.int32)
+    upper = torch.triu(torch.ones(nt, nt, dtype=torch.bool, device="cuda")).repeat_interleave(
+        128, 0).repeat_interleave(128, 1)
+    exact = bool(torch.equal(C[upper], ref[upper]))
+    peak, src = fp8_peak_tflops(torch)
+    achieved = flops / (best / 1e3) / 1e12
+    del A, A01, C, ref, upper
+    torch.cuda.empty_cache()
+    return {"kernel": "k_tile_overlap", "shape": [rows, cols], "density": density,
+            "tiles": tasks, "ms": best, "bound": "tensor", "achieved": achieved,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": src,
+            "flops": flops, "exact_vs_fp32_product": exact}
+
+
+def core_comparison(torch, slg, scale: float = 1.0, s_list=(2, 8, 32)):
+    """Dense core: the lognormal web-shaped hypergraph (4M x 10M, sizes
+    lognormal(2, 1.5) capped 1e5) with a planted core of 4096 hyperedges x
+    8192 vertices at density 0.3; builds on H and H* with and without the
+    tensor-core tile path (identical output)."""
     import hypergen
-    sc = args.core_scale
     t0 = time.perf_counter()
-    h = hypergen.lognormal_web(int(4_000_000 * sc), int(10_000_000 * sc), seed=2)
+    h = hypergen.lognormal_web(int(4_000_000 * scale), int(10_000_000 * scale), seed=2)
     gen_s = time.perf_counter() - t0
     dh = slg.to_device(h)
     rows = {}
     for dual in (False, True):
-        for s in (2, 8, 32):
+        for s in s_list:
             n = slg.count(dh, s, dual, tensor=True)
             o = slg.alloc_outputs(n)
             res = {}
             for tensor in (True, False):
                 slg.build(dh, s, dual=dual, out=o, tensor=tensor)   # warm
+                slg.set_profiling(True)
                 torch.cuda.synchronize()
                 t = time.perf_counter()
                 i, j, w = slg.build(dh, s, dual=dual, out=o, tensor=tensor)
                 torch.cuda.synchronize()
                 ms = (time.perf_counter() - t) * 1e3
+                slg.set_profiling(False)
                 st = slg.last_stats()
                 res["tile" if tensor else "walk"] = {"ms": ms, "wedges_walked": st["wedges"],
-                                                     "core": [st["core_rows"], st["core_cols"]]}
+                                                     "core": [st["core_rows"], st["core_cols"]],
+                                                     "tile_kernel_ms": st["ms_tile"]}
                 if tensor:
                     ref = (i.clone(), j.clone(), w.clone())
                 else:
@@ -743,8 +814,19 @@ def run_core(args):
             res["pairs"] = n
             res["speedup"] = res["walk"]["ms"] / res["tile"]["ms"]
             rows[f"{'H*' if dual else 'H'} s={s}"] = res
-    out = {"mode": "core", "metric": "dense-core tile path vs wedge walk, build ms",
-           "m": h.m, "n": h.n, "nnz": h.nnz, "generate_s": gen_s, "builds": rows}
+            del o, ref, i, j, w
+    out = {"m": h.m, "n": h.n, "nnz": h.nnz, "generate_s": gen_s, "builds": rows}
+    del dh
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_core(args):
+    """--mode core: the dense-core comparison and the tile kernel's roofline."""
+    torch, slg = _setup_gpu()
+    out = {"mode": "core", "metric": "dense-core tile path vs wedge walk, build ms"}
+    out.update(core_comparison(torch, slg, args.core_scale))
+    out["tile_kernel"] = tile_roofline(torch, slg)
     print(json.dumps(out), flush=True)
     return 0
 

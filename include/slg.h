@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define SLG_ABI_VERSION 3
+#define SLG_ABI_VERSION 5
 
 /* Incidence of H as CSR + CSC (Section III: the hyperedge/vertex incidence
  * and its bipartite form).  All pointers are device pointers. */
@@ -394,8 +394,10 @@ int slg_tile_overlap(const uint8_t *A, int32_t rows_pad, int32_t cols_pad,
  *   offsets[g+1])); `offsets` is a HOST array of count + 1 entries (may be
  *   NULL); reads them synchronously.  Returns the device error status of the
  *   last execution, if any.
- * slg_plan_info -- the chosen bin thresholds (warp, CTA small, CTA large
- *   work limits), the tuned build time in ms and the kernels per execution.
+ * slg_plan_info -- the autotuner's choice, in `bins` (6 entries): the warp,
+ *   CTA-small and CTA-large work limits, the sparse bin's upper work limit
+ *   (0: bin off) and lower limit, and the dense-row ratio of the giant bin;
+ *   the tuned build time in ms and the kernels per execution.
  */
 typedef struct slg_plan slg_plan;
 int slg_plan_create(const slg_hypergraph *hs, const int32_t *s, int32_t count,
@@ -474,8 +476,10 @@ typedef struct slg_stats {
   float ms_relabel;        /* SLG_RELABEL_*: building the renumbered side */
   float ms_order;          /* SLG_RELABEL_*: caller ids and (i, j) order */
   int64_t sparse_cycles[5]; /* sparse bin, SM clock cycles summed over CTAs:
-                               row set-up, walk, collect and order the
-                               survivors, emit and clear, staging */
+                               row set-up, first walk, second walk, collect
+                               and order the survivors, emit and clear */
+  float ms_tile;           /* the tensor-core tile kernel of the dense core
+                              (SLG_TENSOR_CORE builds, slg_tile_overlap) */
 } slg_stats;
 
 int slg_last_stats(slg_stats *out);

@@ -89,7 +89,8 @@ class _Stats(ctypes.Structure):
                 ("max_row_work", ctypes.c_int64),
                 ("ms_relabel", ctypes.c_float),
                 ("ms_order", ctypes.c_float),
-                ("sparse_cycles", ctypes.c_int64 * 5)]
+                ("sparse_cycles", ctypes.c_int64 * 5),
+                ("ms_tile", ctypes.c_float)]
 
 
 class _Query(ctypes.Structure):
@@ -597,7 +598,8 @@ def last_stats() -> dict:
             "ms_gather": st.ms_gather, "core_rows": st.core_rows, "core_cols": st.core_cols,
             "core_nnz": st.core_nnz, "giant_cycles": list(st.giant_cycles),
             "max_row_work": st.max_row_work, "ms_relabel": st.ms_relabel,
-            "ms_order": st.ms_order, "sparse_cycles": list(st.sparse_cycles)}
+            "ms_order": st.ms_order, "sparse_cycles": list(st.sparse_cycles),
+            "ms_tile": st.ms_tile}
 
 
 def set_core_params(tau_c: int = 64, tau_r: int = 32, min_density: float = 0.02) -> None:
@@ -658,7 +660,7 @@ class Plan:
             raise SlgError(rc, "slg_plan_execute")
 
     def info(self):
-        b = (ctypes.c_int32 * 3)()
+        b = (ctypes.c_int32 * 6)()
         ms = ctypes.c_float(0)
         n = ctypes.c_int32(0)
         load().slg_plan_info(self._h, ctypes.cast(b, ctypes.c_void_p), ctypes.byref(ms),

@@ -73,7 +73,7 @@ thread_local float t_min_density = 0.02f;
 // Events of one profiled call: plan start, walk (kNumBins + 1), scan end,
 // gather start and end, relabel start and end, re-ordering start and end.
 struct Events {
-  cudaEvent_t ev[kNumBins + 9] = {};
+  cudaEvent_t ev[kNumBins + 11] = {};
   bool on = false;
   explicit Events(bool enable) {
     if (!enable) return;
@@ -97,7 +97,8 @@ struct Events {
 // Event slots.
 constexpr int kEvPlan = 0, kEvWalk = 1, kEvScan = kNumBins + 2, kEvGather0 = kNumBins + 3,
               kEvGather1 = kNumBins + 4, kEvRelabel0 = kNumBins + 5, kEvRelabel1 = kNumBins + 6,
-              kEvOrder0 = kNumBins + 7, kEvOrder1 = kNumBins + 8;
+              kEvOrder0 = kNumBins + 7, kEvOrder1 = kNumBins + 8, kEvTile0 = kNumBins + 9,
+              kEvTile1 = kNumBins + 10;
 
 int status_of(cudaError_t e) {
   if (e == cudaSuccess) return SLG_OK;
@@ -248,6 +249,7 @@ struct Call {
   Op op;
   int32_t *out_i, *out_j, *out_w;
   int32_t *row_work_out;  // slg_row_work: per-row wedge work (device)
+  bool tile_ran;          // the dense-core tile kernel was launched
   int64_t capacity;
   cudaStream_t st;
   DeviceCtx *ctx;
@@ -316,6 +318,8 @@ WalkLaunch walk_launch(Call &c, int mode, int32_t smin, int32_t list_base) {
   L.a.mode = mode;
   L.a.unweighted = c.unweighted;
   L.a.row_s = c.sd.row_s;
+  L.a.row_fhi = c.sd.row_fhi;
+  L.a.dense_ratio = t_bins.dense;
   L.a.smin = smin;
   L.a.row_begin = list_base;
   L.a.n_e = c.w.n_e;
@@ -404,10 +408,13 @@ int plan_core(Call &c, CoreInfo *core) {
   SLG_TRY(c.pool->get(reinterpret_cast<int64_t **>(&tasks), (size_t)(ntile * (ntile + 1) / 2)));
   SLG_TRY(cudaMemsetAsync(A, 0, (size_t)(Mp * Kp), c.st));
   SLG_TRY(launch_core_pack(sd, row_rank, col_rank, A, (int32_t)Kp, w.meta, c.st));
+  if (c.evs->on) cudaEventRecord(c.evs->ev[kEvTile0], c.st);
   cudaError_t e = launch_tile_overlap(A, (int32_t)Mp, (int32_t)Kp, T, tasks, &w.meta->err, c.st);
+  if (c.evs->on) cudaEventRecord(c.evs->ev[kEvTile1], c.st);
   if (e == cudaErrorNotSupported) return SLG_ERR_UNSUPPORTED;
   SLG_TRY(e);
   c.launches += 7;
+  c.tile_ran = true;
   core->row_rank = row_rank;
   core->col_rank = col_rank;
   core->x_off = x_off;
@@ -669,13 +676,14 @@ int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin
         int32_t row_end, Op op, int32_t *out_i, int32_t *out_j, int32_t *out_w,
         int64_t capacity, int64_t *result, cudaStream_t st, const int32_t *row_s = nullptr,
         int32_t *max_row_work = nullptr, long long *row_ptr_out = nullptr,
-        int32_t *row_work_out = nullptr) {
+        int32_t *row_work_out = nullptr, const int32_t *row_fhi = nullptr) {
   int rc = check_args(h, smin, flags);
   if (rc != SLG_OK) return rc;
   if (!result) return SLG_ERR_INVALID;
   Call c = {};
   c.sd = side_of(h, flags);
   c.sd.row_s = row_s;
+  c.sd.row_fhi = row_fhi;
   if (row_begin < 0 || row_end < row_begin || row_end > c.sd.R) return SLG_ERR_INVALID;
   c.smin = smin;
   c.flags = flags;
@@ -704,7 +712,7 @@ int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin
   const int64_t nnz = c.sd.nnz;
   c.R_pad = (int32_t)(((int64_t)c.sd.R + 1023) / 1024 * 1024);
   if (c.R_pad == 0) c.R_pad = 1024;
-  if (c.sd.R > kGiantMaxR) return SLG_ERR_UNSUPPORTED;
+  if (c.sd.R > kMaxRows) return SLG_ERR_UNSUPPORTED;
   const uint32_t relabel = flags & (SLG_RELABEL_ASC | SLG_RELABEL_DESC);
   if (relabel && (row_begin != 0 || row_end != c.sd.R || row_s)) return SLG_ERR_UNSUPPORTED;
 
@@ -819,6 +827,7 @@ int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin
       stats.ms_walk[b] = evs.ms(kEvWalk + kWalkEv[b], kEvWalk + kWalkEv[b] + 1);
     stats.ms_scan = evs.ms(kEvWalk + kNumBins, kEvScan);
     if (op == kOpBuild) stats.ms_gather = evs.ms(kEvGather0, kEvGather1);
+    if (c.tile_ran) stats.ms_tile = evs.ms(kEvTile0, kEvTile1);
     if (perm) {
       stats.ms_relabel = evs.ms(kEvRelabel0, kEvRelabel1);
       if (op == kOpBuild && value > 0) stats.ms_order = evs.ms(kEvOrder0, kEvOrder1);
@@ -869,6 +878,7 @@ struct slg_plan {
   slg_hypergraph u = {};           // the union (device arrays owned below)
   slg::Side sd = {};
   int32_t *row_s_e = nullptr, *row_s_v = nullptr;
+  int32_t *row_fhi_e = nullptr, *row_fhi_v = nullptr;  // end of each row's member
   int32_t *row_base = nullptr;     // [count + 1] first row of each member (side)
   slg::Work w = {};
   int32_t *giant = nullptr;
@@ -911,6 +921,8 @@ cudaError_t enqueue_plan(slg_plan *p, const Bins &bins, cudaStream_t st, int32_t
   L.a.mode = kStage;
   L.a.unweighted = (p->flags & SLG_UNWEIGHTED) != 0;
   L.a.row_s = sd.row_s;
+  L.a.row_fhi = sd.row_fhi;
+  L.a.dense_ratio = bins.dense;
   L.a.smin = 1;
   L.a.row_begin = 0;
   L.a.n_e = w.n_e;
@@ -1366,7 +1378,7 @@ int slg_adjacency(const int32_t *in_i, const int32_t *in_j, const int32_t *in_w,
 
 int slg_components(const int32_t *in_i, const int32_t *in_j, int64_t n, int32_t R,
                    int32_t *labels, int64_t *n_components, void *stream) {
-  if (!n_components || n < 0 || R < 0 || R > kGiantMaxR || (n > 0 && (!in_i || !in_j)) ||
+  if (!n_components || n < 0 || R < 0 || R > kComponentsMaxR || (n > 0 && (!in_i || !in_j)) ||
       (R > 0 && !labels))
     return SLG_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
@@ -1406,13 +1418,22 @@ int slg_tile_overlap(const uint8_t *A, int32_t rows_pad, int32_t cols_pad, int32
   SLG_TRY(pool.get(reinterpret_cast<int64_t **>(&tasks), (size_t)(nt * (nt + 1) / 2)));
   SLG_TRY(pool.get(&err, 1));
   SLG_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
+  Events evs(t_profile != 0);
+  if (evs.on) cudaEventRecord(evs.ev[kEvTile0], st);
   cudaError_t e = launch_tile_overlap(A, rows_pad, cols_pad, C, tasks, err, st);
+  if (evs.on) cudaEventRecord(evs.ev[kEvTile1], st);
   if (e == cudaErrorNotSupported) return SLG_ERR_UNSUPPORTED;
   if (e == cudaErrorInvalidValue) return SLG_ERR_INVALID;
   SLG_TRY(e);
   int32_t h_err = 0;
   SLG_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   SLG_TRY(cudaStreamSynchronize(st));
+  slg_stats stats = {};
+  if (evs.on) {
+    stats.profiled = 1;
+    stats.ms_tile = evs.ms(kEvTile0, kEvTile1);
+  }
+  t_stats = stats;
   return h_err ? SLG_ERR_TIMEOUT : SLG_OK;
 }
 
@@ -1487,6 +1508,8 @@ extern "C" int slg_plan_create(const slg_hypergraph *hs, const int32_t *s, int32
   SLG_TRY(p->mem.get(&v_idx, (size_t)K));
   SLG_TRY(p->mem.get(&p->row_s_e, (size_t)M + 1));
   SLG_TRY(p->mem.get(&p->row_s_v, (size_t)N + 1));
+  SLG_TRY(p->mem.get(&p->row_fhi_e, (size_t)M + 1));
+  SLG_TRY(p->mem.get(&p->row_fhi_v, (size_t)N + 1));
   std::vector<BatchGraph> bg((size_t)count);
   std::vector<int32_t> base((size_t)count + 1);
   int64_t eb = 0, vb = 0, kb = 0;
@@ -1509,16 +1532,18 @@ extern "C" int slg_plan_create(const slg_hypergraph *hs, const int32_t *s, int32
   SLG_TRY(cudaMemcpyAsync(e_off + M, tailv, 4, cudaMemcpyHostToDevice, st));
   SLG_TRY(cudaMemcpyAsync(v_off + N, tailv, 4, cudaMemcpyHostToDevice, st));
   SLG_TRY(launch_concat(bg_d, count, (int32_t)std::min<int64_t>(max_len, 1 << 30), e_off, e_idx,
-                        v_off, v_idx, p->row_s_e, p->row_s_v, st));
+                        v_off, v_idx, p->row_s_e, p->row_s_v, p->row_fhi_e, p->row_fhi_v,
+                        st));
   SLG_TRY(cudaStreamSynchronize(st));
   p->u = slg_hypergraph{(int32_t)M, (int32_t)N, K, e_off, e_idx, v_off, v_idx};
   p->sd = side_of(&p->u, flags);
   p->sd.row_s = dual ? p->row_s_v : p->row_s_e;
+  p->sd.row_fhi = dual ? p->row_fhi_v : p->row_fhi_e;
   // 2. sizes: one counting pass over the union (per-row thresholds)
   int64_t pairs = 0;
   int32_t max_work = 0;
   int rc = run(&p->u, 1, flags, 0, p->sd.R, kOpCount, nullptr, nullptr, nullptr, 0, &pairs, st,
-               p->sd.row_s, &max_work);
+               p->sd.row_s, &max_work, nullptr, nullptr, p->sd.row_fhi);
   if (rc != SLG_OK) return rc;
   p->pairs = pairs;
   // 3. persistent buffers
@@ -1550,8 +1575,17 @@ extern "C" int slg_plan_create(const slg_hypergraph *hs, const int32_t *s, int32
     SLG_TRY(p->mem.get(&p->giant, (size_t)giant_ctas() * (size_t)p->giant_stride));
   }
   // 4. autotuner: bin thresholds, timed on this batch
-  const Bins cands[] = {Bins{}, Bins{64, 1024, 4096}, Bins{128, 512, 4096}, Bins{128, 1024, 2048},
-                        Bins{32, 512, 2048}, Bins{128, 256, 4096}};
+  // candidates: CTA-bin limits, the sparse bin's range (0: off) and the
+  // dense-row ratio of the giant bin
+  const Bins cands[] = {Bins{},
+                        Bins{64, 1024, 4096},
+                        Bins{128, 512, 4096},
+                        Bins{128, 1024, 2048},
+                        Bins{128, 1024, 4096, 8192},
+                        Bins{128, 1024, 4096, 0},
+                        Bins{128, 1024, 2048, 16384, 2048},
+                        Bins{128, 1024, 4096, 16384, 4096, 4},
+                        Bins{128, 1024, 4096, 16384, 4096, 16}};
   cudaEvent_t t0, t1;
   SLG_TRY(cudaEventCreate(&t0));
   SLG_TRY(cudaEventCreate(&t1));
@@ -1660,6 +1694,9 @@ extern "C" int slg_plan_info(const slg_plan *p, int32_t *bins, float *tuned_ms,
     bins[0] = p->bins.warp;
     bins[1] = p->bins.ctas;
     bins[2] = p->bins.ctal;
+    bins[3] = p->bins.sparse;
+    bins[4] = p->bins.bloom;
+    bins[5] = p->bins.dense;
   }
   if (tuned_ms) *tuned_ms = p->tuned_ms;
   if (launches) *launches = p->launches;

@@ -325,6 +325,9 @@ struct Side {
   int64_t nnz;
   const int32_t *r_off, *r_idx, *c_off, *c_idx;
   const int32_t *row_s = nullptr;  // per-row threshold (batched form), else null
+  // per-row bound on far ends (batched form: a row's far ends lie below the
+  // end of its member's rows), else null: R
+  const int32_t *row_fhi = nullptr;
 };
 
 // Threshold of row e: its own (batched form) or the call's s.
@@ -345,10 +348,13 @@ __device__ __forceinline__ int32_t s_of(const int32_t *row_s, int32_t smin, int3
 #ifndef SLG_BLOOM_MIN_WORK
 #define SLG_BLOOM_MIN_WORK 4096
 #endif
+// `dense`: a row with at least one wedge per `dense` ids of its far ends'
+// span is dense (the giant bin counts it in dense windows).
 struct Bins {
   int32_t warp = kWarpMaxWork, ctas = kCtaSMaxWork, ctal = kCtaLMaxWork;
   int32_t sparse = SLG_SPARSE_MAX_WORK;
   int32_t bloom = SLG_BLOOM_MIN_WORK;
+  int32_t dense = kDenseRatio;
 };
 
 // Dense core for the tensor-core tile path (all null / 0 when unused).
@@ -426,6 +432,8 @@ struct EmitArgs {
   int mode;
   int unweighted;
   const int32_t *row_s;               // per-row threshold, or null: smin
+  const int32_t *row_fhi;             // per-row far-end bound, or null: R
+  int32_t dense_ratio;                // Bins::dense
   int full_rows;                      // 1: tails are whole columns, far ends in [0, R)
   const int32_t *row_work;            // [rows] wedges per row (giant bin)
   CoreInfo core;                      // dense core (tile counts added by the giant bin)
@@ -451,11 +459,14 @@ struct WalkLaunch {
   int32_t R;                // rows of the side (far ends lie in [0, R))
 };
 
-// CTAs of the giant kernel (two per SM), of the sparse kernel (one per SM),
-// and the largest side they support.
+// CTAs of the giant kernel (two per SM) and of the sparse kernel.
 int giant_ctas();
 int sparse_ctas();
-constexpr int32_t kGiantMaxR = 1 << 24;
+// The largest side (rows) a build supports: row ids and the giant bin's
+// super-chunk bounds stay below 2^31.
+constexpr int32_t kMaxRows = (int32_t)((1u << 31) - (1u << 23));
+// The largest id space of slg_components (its bounded union-find loop).
+constexpr int32_t kComponentsMaxR = 1 << 24;
 
 // ev (optional): kNumBins + 1 events recorded before the first and after
 // every bin kernel, in launch order (warp, CTA small, CTA large, sparse,
@@ -480,7 +491,8 @@ struct BatchGraph {            // one member, device pointers
 };
 cudaError_t launch_concat(const BatchGraph *g, int32_t count, int32_t max_len, int32_t *e_off,
                           int32_t *e_idx, int32_t *v_off, int32_t *v_idx, int32_t *row_s_e,
-                          int32_t *row_s_v, cudaStream_t st);
+                          int32_t *row_s_v, int32_t *row_fhi_e, int32_t *row_fhi_v,
+                          cudaStream_t st);
 cudaError_t launch_localize(int32_t *out_i, int32_t *out_j, long long pairs,
                             const int32_t *row_base, int32_t count, const long long *row_ptr,
                             long long *offsets, cudaStream_t st);

@@ -21,17 +21,21 @@ __global__ __launch_bounds__(kNT) void k_concat(const BatchGraph *__restrict__ g
                                                 int32_t *__restrict__ v_off,
                                                 int32_t *__restrict__ v_idx,
                                                 int32_t *__restrict__ row_s_e,
-                                                int32_t *__restrict__ row_s_v) {
+                                                int32_t *__restrict__ row_s_v,
+                                                int32_t *__restrict__ row_fhi_e,
+                                                int32_t *__restrict__ row_fhi_v) {
   const BatchGraph g = gs[blockIdx.y];
   const int64_t t0 = (int64_t)blockIdx.x * kNT + threadIdx.x;
   const int64_t step = (int64_t)gridDim.x * kNT;
   for (int64_t i = t0; i < g.m; i += step) {
     e_off[g.e_base + i] = (int32_t)(g.e_off[i] + g.k_base);
     row_s_e[g.e_base + i] = g.s;
+    row_fhi_e[g.e_base + i] = g.e_base + g.m;  // far ends stay inside the member
   }
   for (int64_t i = t0; i < g.n; i += step) {
     v_off[g.v_base + i] = (int32_t)(g.v_off[i] + g.k_base);
     row_s_v[g.v_base + i] = g.s;
+    row_fhi_v[g.v_base + i] = g.v_base + g.n;
   }
   for (int64_t k = t0; k < g.nnz; k += step) {
     e_idx[g.k_base + k] = g.e_idx[k] + g.v_base;
@@ -67,13 +71,15 @@ __global__ __launch_bounds__(kNT) void k_localize(int32_t *__restrict__ out_i,
 
 cudaError_t launch_concat(const BatchGraph *g, int32_t count, int32_t max_len, int32_t *e_off,
                           int32_t *e_idx, int32_t *v_off, int32_t *v_idx, int32_t *row_s_e,
-                          int32_t *row_s_v, cudaStream_t st) {
+                          int32_t *row_s_v, int32_t *row_fhi_e, int32_t *row_fhi_v,
+                          cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   int gx = (max_len + kNT - 1) / kNT;
   if (gx < 1) gx = 1;
   if (gx > 1024) gx = 1024;
   dim3 grid(gx, count);
-  k_concat<<<grid, kNT, 0, st>>>(g, e_off, e_idx, v_off, v_idx, row_s_e, row_s_v);
+  k_concat<<<grid, kNT, 0, st>>>(g, e_off, e_idx, v_off, v_idx, row_s_e, row_s_v, row_fhi_e,
+                                 row_fhi_v);
   return cudaGetLastError();
 }
 

@@ -266,7 +266,8 @@ __global__ __launch_bounds__(kRowsNT) void k_rows_work(Side s, int32_t smin, int
       // its span (f in (e, R))
       if (!forced && my_work > bins.bloom && my_work <= bins.sparse &&
           s_of(s.row_s, smin, e) >= 2 &&
-          (my_bin != kBinGiant || (long long)my_work * kDenseRatio < (long long)(s.R - 1 - e)))
+          (my_bin != kBinGiant ||
+           (long long)my_work * bins.dense < (long long)((s.row_fhi ? s.row_fhi[e] : s.R) - 1 - e)))
         my_bin = kBinSparse;
       if (my_bin == kBinGiant) atomicMax(&meta->max_giant_work, my_work);
       if (my_bin == kBinSparse) atomicMax(&meta->max_sparse_work, my_work);

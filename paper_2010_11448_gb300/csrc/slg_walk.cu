@@ -684,14 +684,17 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
     if (e < 0) break;
     const int32_t smin = s_of(a.row_s, a.smin, e);
     const int32_t f_lo = a.full_rows ? 0 : e + 1;
-    const int32_t span = R - f_lo;
+    // far ends lie in [f_lo, f_hi): below R, or below the end of e's member
+    // in a batched union
+    const int32_t f_hi = a.row_fhi ? a.row_fhi[e] : R;
+    const int32_t span = f_hi - f_lo;
     const int shift = min(kShiftMax, max(0, ceil_log2(span) - kNSBLog));
     const int32_t chunk_w = kNSB << shift;  // ids per super-chunk
     const int32_t cap = kGiantTMax / 2 - (1 << shift);
     const int32_t work = a.row_work[e - a.row_begin];
     // Dense rows (at least one wedge per 8 ids) count fixed windows of
     // kDenseW ids in a dense shared array: no hashing, no sort.
-    const bool dense = (long long)work * kDenseRatio >= (long long)span;
+    const bool dense = (long long)work * a.dense_ratio >= (long long)span;
     if (work > q4) {  // the scratch is sized by the largest row: cannot happen
       if (threadIdx.x == 0) raise_error(meta, SLG_ERR_INVALID, kWhereGiant);
       break;
@@ -741,7 +744,7 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
       long long clk0 = clock64();
       // 1. flattened far ends; a row within one super-chunk also counts its
       // sub-range histogram here (saving one pass over the copy)
-      const bool single = R - f_lo <= chunk_w;
+      const bool single = f_hi - f_lo <= chunk_w;
       if (single) {
         for (int i = threadIdx.x; i < kNSB; i += kGiantNT) {
           sub[i] = 0;
@@ -759,13 +762,13 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
       }
       long long clk_part = 0, clk_bucket = 0;
       if (threadIdx.x == 0) atomicAdd(&meta->giant_cycles[0], (unsigned long long)(clock64() - clk0));
-      for (int32_t F0 = f_lo; F0 < R; F0 += chunk_w) {
+      for (int32_t F0 = f_lo; F0 < f_hi; F0 += chunk_w) {
         // An empty bucket is skipped without a barrier, so threads may still
         // be reading the previous super-chunk's sub[] / bstart[] here: every
         // thread must be done with them before they are rewritten.
         __syncthreads();
         const long long c0 = clock64();
-        const int32_t F1 = (R - F0 > chunk_w) ? F0 + chunk_w : R;
+        const int32_t F1 = (f_hi - F0 > chunk_w) ? F0 + chunk_w : f_hi;
         const int32_t nsb = ((F1 - F0 - 1) >> shift) + 1;
         // 2. histograms of sub-ranges (wedges; tile items), scans, scatter
         if (!single) {
