@@ -675,7 +675,8 @@ def run_serve(args):
                for _ in range(n)]
     runs = {}
     for reuse in (False, True):
-        srv = Server(dhs, slots=4, memory_budget=96 << 30, reuse=reuse, cache_bytes=48 << 30)
+        srv = Server(dhs, slots=4, memory_budget=96 << 30, reuse=reuse, cache_bytes=64 << 30,
+                     base_s=2)
         t0 = time.perf_counter()
         due = t0
         queries = []
@@ -689,7 +690,7 @@ def run_serve(args):
             q.wait()
         wall = time.perf_counter() - t0
         srv.close()
-        runs["reuse" if reuse else "walk_every_query"] = Server.summary(queries, wall)
+        runs["base_lists" if reuse else "walk_every_query"] = Server.summary(queries, wall)
         del srv, queries
         torch.cuda.empty_cache()
     torch.cuda.empty_cache()

@@ -290,7 +290,9 @@ def build(h: DeviceHypergraph, s: int, dual=False, unweighted=False,
                           oj.data_ptr(), ow.data_ptr() if ow is not None else None,
                           cap, ctypes.byref(n), _stream(stream))
     if rc != 0:
-        raise SlgError(rc, "slg_build")
+        err = SlgError(rc, "slg_build")
+        err.needed = int(n.value)  # |L_s| when the capacity was too small
+        raise err
     p = int(n.value)
     return oi[:p], oj[:p], (ow[:p] if ow is not None else None)
 

@@ -9,32 +9,43 @@ others run on theirs, so their kernels overlap on the GPU.  A query that
 arrives while others are on the GPU is admitted as soon as a slot and the
 memory are free.  Latency is measured from submission to completion.
 
-Reuse across thresholds (``reuse=True``): L_s is the sub-list of any L_s'
-with s' <= s and w >= s (Section III), so per hypergraph and side the
-server keeps the list of the smallest threshold built so far (within
-``cache_bytes``) and answers any larger threshold by filtering it
-(slg_filter) instead of walking again.
+One walk per query: the output is sized from what the server already knows
+(the query's own pair count from an earlier identical query, else the count
+of the same graph and side at the nearest smaller threshold -- L_s is the
+part of L_s' with w >= s for s' <= s (Section III), so that count bounds it
+-- else a first guess), and a build whose list does not fit returns its
+exact size and is run once more at that size.
 
-All computation runs in the library's CUDA kernels (slg_count / slg_build
+Reuse across thresholds (``reuse=True``): per hypergraph and side the server
+keeps one base list L_{base_s} (within ``cache_bytes``), built by the first
+query with s >= base_s on that graph and side, and answers every query with
+s >= base_s by filtering it (slg_filter) instead of walking again.
+``base_s=None`` keeps instead the list of the smallest threshold queried so
+far.
+
+All computation runs in the library's CUDA kernels (slg_build / slg_filter
 through the binding); this module only schedules.
 """
 from __future__ import annotations
 
+import bisect
 import collections
 import threading
 import time
 
 import numpy as np
 
-from . import (DeviceHypergraph, SlgError, alloc_outputs, build, count, filter_pairs,
-               last_stats, wedges)
+from . import (DeviceHypergraph, SlgError, alloc_outputs, build, filter_pairs, last_stats,
+               wedges)
+
+_FIRST_GUESS = 1 << 24  # pairs, when nothing bounds a query's list yet
 
 
 class Query:
     """One request and its outcome."""
 
     __slots__ = ("gid", "s", "dual", "t_submit", "t_start", "t_done", "pairs", "result",
-                 "error", "est_bytes", "reused", "_done")
+                 "error", "est_bytes", "reused", "walks", "_done")
 
     def __init__(self, gid: int, s: int, dual: bool):
         self.gid, self.s, self.dual = gid, s, dual
@@ -44,6 +55,7 @@ class Query:
         self.error = None
         self.est_bytes = 0
         self.reused = False
+        self.walks = 0
         self._done = threading.Event()
 
     def wait(self, timeout=None) -> bool:
@@ -59,20 +71,22 @@ class Server:
 
     def __init__(self, graphs: list[DeviceHypergraph], slots: int = 4,
                  memory_budget: int = 64 << 30, keep_results: bool = False,
-                 reuse: bool = False, cache_bytes: int = 32 << 30):
+                 reuse: bool = False, cache_bytes: int = 32 << 30, base_s: int | None = 2):
         import torch
         self.graphs = graphs
         self.keep = keep_results
         self.reuse = reuse
+        self.base_s = base_s
         self.cache_bytes = int(cache_bytes)
         self.cached = {}     # (gid, dual) -> (s, (i, j, w), bytes)
+        self.building = {}   # (gid, dual) -> threading.Event while its base list is built
         self.cache_used = 0
         self.budget = int(memory_budget)
         self.in_flight = 0
         self.pending = collections.deque()
         self.cv = threading.Condition()
         self.closed = False
-        self.pair_cache: dict = {}
+        self.counts: dict = {}  # (gid, dual) -> sorted [(s, |L_s|)]
         self.done: list[Query] = []
         # per graph and side: incidences, rows, columns, largest row work at
         # s = 1 (an upper bound for every s), for the memory estimate
@@ -88,6 +102,23 @@ class Server:
         for t in self.workers:
             t.start()
 
+    # ------------------------------------------------------ counts, bounds --
+    def _known(self, gid: int, dual: bool, s: int, n: int):
+        with self.cv:
+            lst = self.counts.setdefault((gid, dual), [])
+            k = bisect.bisect_left(lst, (s, -1))
+            if k < len(lst) and lst[k][0] == s:
+                return
+            lst.insert(k, (s, n))
+
+    def _bound(self, gid: int, dual: bool, s: int):
+        """|L_s| if known, else |L_s'| for the largest known s' < s (an upper
+        bound), else None."""
+        with self.cv:
+            lst = self.counts.get((gid, dual), [])
+            k = bisect.bisect_right(lst, (s, 1 << 62))
+            return lst[k - 1][1] if k else None
+
     # ----------------------------------------------------------- estimates --
     def _estimate(self, q: Query) -> int:
         base = self._cached_for(q)
@@ -95,10 +126,17 @@ class Server:
             return 2 * base[2] + 8 * (base[1][0].shape[0] // 8192 + 2)
         nnz, rows, cols, maxw = self.shape[(q.gid, q.dual)]
         work = 4 * (7 * nnz + 12 * rows + cols)            # planning arrays
-        giant = 152 * 16 * maxw                             # giant-bin scratch bound
-        pairs = self.pair_cache.get((q.gid, q.s, q.dual))
-        out = 20 * (pairs if pairs is not None else 2 * nnz)
+        giant = 304 * 16 * maxw                             # giant-bin scratch bound
+        s = self._base_for(q) or q.s
+        pairs = self._bound(q.gid, q.dual, s)
+        out = 20 * (pairs if pairs is not None else _FIRST_GUESS)
         return work + giant + out
+
+    def _base_for(self, q: Query):
+        """The base threshold this query's answer comes from, or None."""
+        if self.reuse and self.base_s is not None and q.s >= self.base_s:
+            return self.base_s
+        return None
 
     def _cached_for(self, q: Query):
         if not self.reuse:
@@ -106,20 +144,21 @@ class Server:
         e = self.cached.get((q.gid, q.dual))
         return e if e is not None and e[0] <= q.s else None
 
-    def _keep_list(self, q: Query, res):
-        """Keep `res` = L_{q.s} if it is the smallest threshold of its graph
-        and side so far and fits the cache."""
+    def _keep_list(self, gid: int, dual: bool, s: int, res) -> bool:
+        """Keep `res` = L_s as the list of its graph and side if it has the
+        smallest threshold so far and fits the cache."""
         nbytes = 12 * int(res[0].shape[0])
         with self.cv:
-            key = (q.gid, q.dual)
+            key = (gid, dual)
             old = self.cached.get(key)
-            if old is not None and old[0] <= q.s:
-                return
+            if old is not None and old[0] <= s:
+                return False
             free = self.cache_bytes - self.cache_used + (old[2] if old else 0)
             if nbytes > free:
-                return
-            self.cached[key] = (q.s, res, nbytes)
+                return False
+            self.cached[key] = (s, res, nbytes)
             self.cache_used += nbytes - (old[2] if old else 0)
+            return True
 
     # ----------------------------------------------------------------- API --
     def submit(self, gid: int, s: int, dual: bool = False) -> Query:
@@ -153,6 +192,78 @@ class Server:
                     return None
                 self.cv.wait(0.05)
 
+    def _walk(self, q: Query, s: int, st):
+        """L_s of the query's graph and side in one walk (two when the first
+        guess of its size was too small)."""
+        g = self.graphs[q.gid]
+        n = self._bound(q.gid, q.dual, s)
+        cap = n if n is not None else _FIRST_GUESS
+        for attempt in (0, 1):
+            out = alloc_outputs(max(cap, 1), False, g.e_off.device)
+            q.walks += 1
+            try:
+                res = build(g, s, dual=q.dual, out=out, stream=st)
+                self._known(q.gid, q.dual, s, int(res[0].shape[0]))
+                return res
+            except SlgError as exc:
+                if exc.status != 2 or attempt:
+                    raise
+                cap = exc.needed            # the exact size, counted by the walk
+                self._known(q.gid, q.dual, s, cap)
+                del out
+
+    def _base_list(self, q: Query, st):
+        """The kept base list of the query's graph and side, built now if it
+        is missing (other queries on the same graph and side wait for it)."""
+        key = (q.gid, q.dual)
+        while True:
+            with self.cv:
+                e = self.cached.get(key)
+                if e is not None and e[0] <= q.s:
+                    return e[1]
+                ev = self.building.get(key)
+                if ev is None:
+                    ev = threading.Event()
+                    self.building[key] = ev
+                    mine = True
+                else:
+                    mine = False
+            if not mine:
+                ev.wait()
+                with self.cv:
+                    e = self.cached.get(key)
+                if e is None or e[0] > q.s:
+                    return None          # not kept (cache full): walk instead
+                return e[1]
+            try:
+                res = self._walk(q, self.base_s, st)
+                st.synchronize()
+                kept = self._keep_list(q.gid, q.dual, self.base_s, res)
+                return res
+            finally:
+                with self.cv:
+                    del self.building[key]
+                ev.set()
+
+    def _answer(self, q: Query, st):
+        import torch
+        with torch.cuda.stream(st):
+            if self.reuse:
+                base = None
+                if self._base_for(q) is not None:
+                    base = self._base_list(q, st)
+                else:
+                    e = self._cached_for(q)
+                    base = e[1] if e is not None else None
+                if base is not None:
+                    q.reused = True
+                    return filter_pairs(*base, q.s, stream=st)
+            res = self._walk(q, q.s, st)
+            if self.reuse and self.base_s is None:
+                st.synchronize()
+                self._keep_list(q.gid, q.dual, q.s, res)
+            return res
+
     def _worker(self, k: int):
         import torch
         st = self.streams[k]
@@ -162,36 +273,19 @@ class Server:
                 return
             q.t_start = time.perf_counter()
             try:
-                g = self.graphs[q.gid]
-                key = (q.gid, q.s, q.dual)
                 for attempt in (0, 1):
-                    with self.cv:
-                        base = self._cached_for(q)
                     try:
-                        with torch.cuda.stream(st):
-                            if base is not None:
-                                i, j, w = filter_pairs(*base[1], q.s, stream=st)
-                                q.reused = True
-                            else:
-                                n = self.pair_cache.get(key)
-                                if n is None:
-                                    n = count(g, q.s, q.dual, stream=st)
-                                    self.pair_cache[key] = n
-                                out = alloc_outputs(n, False, g.e_off.device)
-                                i, j, w = build(g, q.s, dual=q.dual, out=out, stream=st)
-                            st.synchronize()
+                        i, j, w = self._answer(q, st)
+                        st.synchronize()
                         break
                     except (SlgError, torch.cuda.OutOfMemoryError) as exc:
                         # out of device memory: give the kept lists back, retry once
                         if attempt or getattr(exc, "status", 3) != 3 or not self.reuse:
                             raise
-                        base = out = None
                         with self.cv:
                             self.cached.clear()
                             self.cache_used = 0
                         torch.cuda.empty_cache()
-                if self.reuse and base is None:
-                    self._keep_list(q, (i, j, w))
                 q.pairs = int(i.shape[0])
                 if self.keep:
                     q.result = (i, j, w)
@@ -213,6 +307,7 @@ class Server:
                 "first_error": (f"{errs[0].gid}/{errs[0].s}/{errs[0].dual}: {errs[0].error!r}"
                                 if errs else None),
                 "answered_by_filter": sum(q.reused for q in queries),
+                "walks": sum(q.walks for q in queries),
                 "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
                 "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
                 "mean_ms": float(lat.mean()) if lat.size else None,

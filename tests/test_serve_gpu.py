@@ -73,7 +73,7 @@ def test_reuse_filters_equal_walks(pool):
     from paper_2010_11448_gb300.serve import Server
     hs, dhs = pool
     reqs = [(g, s, d) for s in (1, 3, 2, 5, 8, 4) for g in (0, 2) for d in (False, True)]
-    srv = Server(dhs, slots=2, keep_results=True, reuse=True)
+    srv = Server(dhs, slots=2, keep_results=True, reuse=True, base_s=None)
     qs = []
     for r in reqs:
         q = srv.submit(*r)
@@ -86,3 +86,29 @@ def test_reuse_filters_equal_walks(pool):
     # s = 1 is built first for every graph and side; all later ones filter
     assert [q.reused for q in qs] == [False] * 4 + [True] * (len(reqs) - 4)
     assert Server.summary(qs, 1.0)["answered_by_filter"] == len(reqs) - 4
+
+
+def test_eager_base_lists_equal_walks(pool):
+    # base_s = 2: the first query with s >= 2 on a graph and side builds L_2
+    # and keeps it; every query with s >= 2 is answered by filtering it, s = 1
+    # walks; concurrent queries on the same graph wait for the one base build
+    from paper_2010_11448_gb300.serve import Server
+    hs, dhs = pool
+    rng = np.random.default_rng(3)
+    reqs = [(int(rng.integers(0, 4)), int(rng.integers(1, 12)), bool(rng.integers(0, 2)))
+            for _ in range(60)]
+    srv = Server(dhs, slots=4, keep_results=True, reuse=True, base_s=2)
+    qs = [srv.submit(*r) for r in reqs]
+    for q in qs:
+        assert q.wait(300)
+    srv.close()
+    for (gid, s, dual), q in zip(reqs, qs):
+        assert q.error is None
+        assert np.array_equal(as_np(q.result), as_np(slg.build(dhs[gid], s, dual=dual)))
+        assert q.reused == (s >= 2)
+    st = Server.summary(qs, 1.0)
+    keys = {(g, d) for g, s, d in reqs if s >= 2}
+    ones = sum(1 for _, s, _ in reqs if s == 1)
+    # one base build per graph and side (two walks at most when the first
+    # size guess was short), one walk per s = 1 query (two at most)
+    assert st["walks"] <= 2 * (len(keys) + ones)
