@@ -660,6 +660,9 @@ def run_serve(args):
     recipe scaled 0.05x-1x, geometric), a Poisson stream of queries (graph
     U{0..15}, s U{1..64}, side Bernoulli(0.5)) at `rate` per second."""
     import numpy as np
+    # lists of very different sizes come and go: let torch's allocator grow
+    # and shrink its segments instead of keeping fragments
+    os.environ.setdefault("PYTORCH_CUDA_ALLOC_CONF", "expandable_segments:True")
     torch, slg = _setup_gpu()
     import hypergen
     from paper_2010_11448_gb300.serve import Server
@@ -675,7 +678,7 @@ def run_serve(args):
                for _ in range(n)]
     runs = {}
     for reuse in (False, True):
-        srv = Server(dhs, slots=4, memory_budget=96 << 30, reuse=reuse, cache_bytes=64 << 30,
+        srv = Server(dhs, slots=4, memory_budget=96 << 30, reuse=reuse, cache_bytes=48 << 30,
                      base_s=2)
         t0 = time.perf_counter()
         due = t0
@@ -690,6 +693,7 @@ def run_serve(args):
             q.wait()
         wall = time.perf_counter() - t0
         srv.close()
+        slg.release_memory()
         runs["base_lists" if reuse else "walk_every_query"] = Server.summary(queries, wall)
         del srv, queries
         torch.cuda.empty_cache()

@@ -496,6 +496,13 @@ int slg_last_stats(slg_stats *out);
  */
 int slg_set_core_params(int32_t tau_c, int32_t tau_r, float min_density);
 
+/* Returns the device memory that the library keeps for later calls on the
+ * current device (its stream-ordered pool of working buffers) to the
+ * system, after waiting for the device.  For processes where another
+ * allocator (a framework's caching allocator) needs that memory.  Not a
+ * paper operation: a library service. */
+int slg_release_memory(void);
+
 /* Per-phase CUDA-event timing of later calls from this host thread
  * (enable = 1) or not (0, the default).  Events are recorded on the call's
  * stream; the times land in slg_stats.ms_*. */

@@ -127,6 +127,7 @@ ABI_FUNCTIONS = {
     "slg_row_offsets": (ctypes.c_int, [_HP, ctypes.c_int32, ctypes.c_uint32, _VP, _VP]),
     "slg_last_stats": (ctypes.c_int, [ctypes.POINTER(_Stats)]),
     "slg_set_profiling": (ctypes.c_int, [ctypes.c_int]),
+    "slg_release_memory": (ctypes.c_int, []),
     "slg_set_core_params": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_float]),
     "slg_tile_overlap": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _VP, _VP]),
     "slg_filter": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_int32, _VP, _VP,
@@ -708,6 +709,13 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def release_memory() -> None:
+    """Give the library's cached device memory back (slg_release_memory)."""
+    rc = load().slg_release_memory()
+    if rc != 0:
+        raise SlgError(rc, "slg_release_memory")
 
 
 def set_profiling(enable: bool) -> None:

@@ -1437,6 +1437,16 @@ int slg_tile_overlap(const uint8_t *A, int32_t rows_pad, int32_t cols_pad, int32
   return h_err ? SLG_ERR_TIMEOUT : SLG_OK;
 }
 
+int slg_release_memory(void) {
+  cudaMemPool_t m = lib_pool();
+  if (!m) return SLG_OK;
+  if (cudaDeviceSynchronize() != cudaSuccess || cudaMemPoolTrimTo(m, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return SLG_ERR_CUDA;
+  }
+  return SLG_OK;
+}
+
 int slg_set_core_params(int32_t tau_c, int32_t tau_r, float min_density) {
   if (tau_c < 1 || tau_r < 1 || !(min_density > 0.f && min_density <= 1.f))
     return SLG_ERR_INVALID;

@@ -526,6 +526,137 @@ __global__ __launch_bounds__(NT, MINB) void k_walk_cta(Walk w, const int32_t *__
   }
 }
 
+// ------------------------------------------------------------ sparse bin --
+//
+// Large rows whose far ends are sparse in their id span, with s >= 2.  Almost
+// every far end of such a row occurs once (on the Chung-Lu workloads about
+// 96 % of the wedges of these rows are the only wedge to their far end), and
+// a far end with a single wedge can never reach s >= 2.  The row is counted
+// in two walks with little shared memory, so that several rows are in
+// flight on each SM (the walk's far-end gathers are latency-bound: a row at
+// a time per SM leaves the memory system idle):
+//   1. every wedge sets its far end's bit in a one-hash Bloom filter (one
+//      shared atomicOr); a wedge that finds the bit already set makes f a
+//      candidate: f is claimed in a small shared table (key, count 0) and
+//      marked in a second filter.  Every f with two or more wedges becomes
+//      a candidate (its second wedge finds the bit set); so may a few
+//      single-wedge f whose bit another f had set;
+//   2. a second walk counts, exactly, every wedge whose far end is a
+//      candidate (the second filter screens out almost all others before
+//      the table is probed).  The count of f is then |e ∩ f|.
+// The candidates with count >= s are sorted and emitted.  A row of at most
+// kSpCache wedges keeps its far ends in shared memory during the first walk
+// and reads them from there in the second.  A row whose candidates overflow
+// the table (a probe sequence longer than kSpMaxProbe) is handed to the
+// giant bin, which runs after this one.
+
+#ifndef SLG_SP_NT
+#define SLG_SP_NT 256
+#endif
+#ifndef SLG_SP_LOGB
+#define SLG_SP_LOGB 17
+#endif
+#ifndef SLG_SP_LGT
+#define SLG_SP_LGT 12
+#endif
+#ifndef SLG_SP_CACHE
+#define SLG_SP_CACHE 0
+#endif
+#ifndef SLG_SP_MINB
+#define SLG_SP_MINB 4
+#endif
+#ifndef SLG_SP_G
+#define SLG_SP_G 6
+#endif
+#ifndef SLG_SP_RUNS
+#define SLG_SP_RUNS 1  // order survivor sets above 64 by sorted warp runs
+#endif
+constexpr int kSpNT = SLG_SP_NT;
+constexpr int kSpLogB = SLG_SP_LOGB;          // Bloom filter bits (log2)
+constexpr int kSpWords = 1 << (kSpLogB - 5);
+constexpr int kSpCWords = kSpWords / 4;       // candidate filter words
+constexpr int kSpLgT = SLG_SP_LGT;
+constexpr int kSpT = 1 << kSpLgT;             // candidate table slots
+constexpr int kSpCache = SLG_SP_CACHE;        // far ends kept of a small row
+constexpr int kSpMaxProbe = 32;
+constexpr int kSpG = SLG_SP_G;                // wedges per thread per walk step
+constexpr int kSpSPT = kSpT / kSpNT;          // table slots per thread
+static_assert(kSpSPT >= 1 && kSpWords % (4 * kSpNT) == 0 && kSpCWords % 4 == 0,
+              "sparse bin geometry");
+
+// [s_base 8][s_ovf 4][s_row 4][pad 16][filter kSpWords x 4]
+// [candidate filter kSpCWords x 4][table kSpT x 8][cache kSpCache x 4]
+// [s_beg NT][s_pref NT+1][ws NT/32+1]
+constexpr size_t sparse_smem() {
+  return 32 + (size_t)kSpWords * 4 + (size_t)kSpCWords * 4 + (size_t)kSpT * 8 +
+         (size_t)kSpCache * 4 + (size_t)(2 * kSpNT + 1 + kSpNT / 32 + 1) * 4;
+}
+
+// A row's filter has 2^lgb bits (its candidate filter 2^(lgb - 2)) and its
+// table 2^lgt slots, sized by the row's work (see sp_sizes).
+__device__ __forceinline__ uint32_t sp_h1(int32_t f, int lgb) {  // Bloom filter bit
+  return ((uint32_t)f * 0x9E3779B1u) >> (32 - lgb);
+}
+__device__ __forceinline__ uint32_t sp_h2(int32_t f, int lgb) {  // candidate filter bit
+  return ((uint32_t)f * 0x85EBCA6Bu) >> (34 - lgb);
+}
+__device__ __forceinline__ uint32_t sp_ht(int32_t f, int lgt) {  // candidate table slot
+  return ((uint32_t)f * 0xC2B2AE35u) >> (32 - lgt);
+}
+
+// Per-row sizes: a filter of >= 32 bits per wedge (so that a single-wedge
+// far end finds its bit set by another with probability below 1/64 on
+// average) and a table of >= one slot per wedge (every candidate has two
+// wedges or is such a collision), within the shared-memory maxima.
+__device__ __forceinline__ void sp_sizes(int32_t work, int *lgb, int *lgt) {
+  const int lw = ceil_log2(work > 1 ? work : 2);
+  *lgb = min(max(lw + 5, 12), kSpLogB);
+  *lgt = min(max(lw, 7), kSpLgT);
+}
+
+// Pass 1: f is a candidate (its filter bit was already set).  Claims f's
+// table slot (32-bit CAS on the key word; the count word stays 0) unless it
+// is there already, and marks it in the candidate filter.  A probe sequence
+// longer than kSpMaxProbe marks the row as overflowed.
+__device__ __forceinline__ void sp_candidate(unsigned long long *tab, uint32_t *cand, int32_t f,
+                                             int32_t *s_ovf, int lgb, int lgt) {
+  if (*(volatile int32_t *)s_ovf) return;
+  const uint32_t mask = (1u << lgt) - 1u;
+  uint32_t h = sp_ht(f, lgt);
+  for (int probe = 0; probe < kSpMaxProbe; ++probe) {
+    const uint32_t k = atomicCAS(count_word(tab, h) + 1, 0xFFFFFFFFu, (uint32_t)f);
+    if (k == 0xFFFFFFFFu) {
+      const uint32_t c = sp_h2(f, lgb);
+      atomicOr(cand + (c >> 5), 1u << (c & 31));
+      return;
+    }
+    if (k == (uint32_t)f) return;
+    h = (h + 1) & mask;
+  }
+  *(volatile int32_t *)s_ovf = 1;
+}
+
+// Pass 2: one wedge to f; counted when f is a candidate.  Unweighted: a
+// count that reached s is not raised further.
+__device__ __forceinline__ void sp_count(unsigned long long *tab, const uint32_t *cand,
+                                         int32_t f, int32_t smin, bool unweighted, int lgb,
+                                         int lgt) {
+  const uint32_t c = sp_h2(f, lgb);
+  if (!(cand[c >> 5] & (1u << (c & 31)))) return;
+  const uint32_t mask = (1u << lgt) - 1u;
+  uint32_t h = sp_ht(f, lgt);
+  for (int probe = 0; probe < kSpMaxProbe; ++probe) {
+    uint32_t *cw = count_word(tab, h);
+    const uint32_t k = cw[1];
+    if (k == (uint32_t)f) {
+      if (!unweighted || (int32_t)*(volatile uint32_t *)cw < smin) atomicAdd(cw, 1u);
+      return;
+    }
+    if (k == 0xFFFFFFFFu) return;
+    h = (h + 1) & mask;
+  }
+}
+
 // ------------------------------------------------------------- giant bin --
 //
 // A CTA takes one giant row at a time (dynamic ticket; rows above
@@ -581,6 +712,15 @@ constexpr int kGiantG = 6;  // wedges per thread per step of the giant bin's wal
 static_assert(kGiantDirectMax <= kGiantTMax && kGiantDirectMax / 2 <= kGiantList,
               "a direct row fits the table and the survivor list");
 constexpr int kGiantQ = kGiantList / kGiantNT;
+// Bloom-counted buckets (s >= 2, sparse rows): at most this many wedges; the
+// filter takes the survivor-list area (2^kGiantLogB bits).
+#ifndef SLG_GIANT_BLOOM_CAP
+#define SLG_GIANT_BLOOM_CAP 12288
+#endif
+constexpr int32_t kGiantBloomCap = SLG_GIANT_BLOOM_CAP;
+constexpr int kGiantLogB = 17;
+static_assert((1 << (kGiantLogB - 3)) <= kGiantList * 4, "the filter fits the list area");
+static_assert((1 << (kGiantLogB - 7)) <= kNSB, "the candidate filter fits the item area");
 
 // [s_base 16][s_misc 16][table TMAX x 8][sub NSB][subt NSB+1][bstart NSB+1]
 // [s_beg NT][s_pref NT+1][ws NT/32+1][list kGiantList][list count 1]
@@ -649,6 +789,7 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
   if (meta->err) return;
   extern __shared__ __align__(16) unsigned char smem[];
   long long *s_base = reinterpret_cast<long long *>(smem);
+  int32_t *s_x = reinterpret_cast<int32_t *>(smem + 8);      // [0] overflow, [1] boundary
   int32_t *s_misc = reinterpret_cast<int32_t *>(smem + 16);  // [0] row, [1] buckets, [2,3] items
   unsigned long long *tab = reinterpret_cast<unsigned long long *>(smem + 32);
   int32_t *sub = reinterpret_cast<int32_t *>(tab + kGiantTMax);
@@ -690,7 +831,7 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
     const int32_t span = f_hi - f_lo;
     const int shift = min(kShiftMax, max(0, ceil_log2(span) - kNSBLog));
     const int32_t chunk_w = kNSB << shift;  // ids per super-chunk
-    const int32_t cap = kGiantTMax / 2 - (1 << shift);
+    const int32_t cap_hash = kGiantTMax / 2 - (1 << shift);
     const int32_t work = a.row_work[e - a.row_begin];
     // Dense rows (at least one wedge per 8 ids) count fixed windows of
     // kDenseW ids in a dense shared array: no hashing, no sort.
@@ -703,6 +844,11 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
     // core row f > e with a non-zero tile count.
     const CoreInfo &ci = a.core;
     const bool core_row = ci.T && ci.row_rank[e + 1] != ci.row_rank[e];
+    // Sparse buckets with s >= 2 are counted in two passes with a Bloom
+    // filter (as the sparse bin counts rows), so they can hold kGiantBloomCap
+    // wedges instead of what a table of their distinct far ends allows.
+    const bool bloom_row = smin >= 2 && !dense && !core_row;
+    const int32_t cap = bloom_row ? kGiantBloomCap : cap_hash;
     const int32_t ri = core_row ? ci.row_rank[e] : 0;
     const int32_t *Trow = core_row ? ci.T + (long long)ri * ci.Mp : nullptr;
     long long base = -1;
@@ -903,54 +1049,123 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
             __syncthreads();
             continue;
           }
-          const int32_t width = (b1 - b0) << shift;
-          const int lgT = table_lg(min(hi - lo + nit, width), lg_max);
-          const int32_t T = 1 << lgT;
-          // s >= 2: survivors listed as they appear; s = 1: every key survives
-          const bool list = smin >= 2;
-          auto insert_all = [&](auto list_tag) {
-            constexpr bool L = decltype(list_tag)::value;
-            for_each_batched<kGiantNT, 8>(wl, lo, hi, [&](int32_t f) {
-              table_insert<L>(tab, lgT, f, 1, smin, unweighted, meta, sl);
-            });
-            if (core_row && nit > 0)
-              for (int32_t p = s_misc[2] + (int32_t)threadIdx.x; p < s_misc[3]; p += kGiantNT) {
-                const int32_t f = ci.core_list[p];
-                const int32_t wt = Trow[p];
-                if (wt > 0 && w.r_off[f + 1] - w.r_off[f] >= smin)
-                  table_insert<L>(tab, lgT, f, wt, smin, unweighted, meta, sl);
-              }
-          };
-          int32_t at = 0, used = T, total;
-          if (list) {
-            insert_all(std::true_type{});
-            total = table_collect_list<kGiantNT, kGiantQ>(tab, T, sl, emit, &at, &used);
-          } else {
-            insert_all(std::false_type{});
-            __syncthreads();
-            total = table_collect<kGiantNT, kGiantSPT>(tab, T, smin, emit, ws, &at, &used);
-          }
-          if (a.mode == kStage && out + total > q4) {
-            // staged pairs would not fit the scratch (sized by wedges + core
-            // items): report instead of writing past it
-            if (threadIdx.x == 0) raise_error(meta, SLG_ERR_INVALID, kWhereGiant);
-            table_reset_front<kGiantNT>(tab, used);
-            break;
-          }
-          if (emit && total > 0) {
-            for (int32_t i = threadIdx.x; i < total; i += kGiantNT) {
-              const unsigned long long x = tab[at + i];
-              const int32_t f = (int32_t)(x >> 32), n = (int32_t)(uint32_t)x;
-              if (a.mode == kDirect) {
-                put(a, base, out + i, e, f, n);
-              } else {
-                tj[out + i] = f;
-                if (!unweighted) tw[out + i] = n;
+          // the sorted pairs tab[at, at + total) of a bucket go to the row's
+          // output; false (uniform) when they would not fit the scratch
+          auto emit_sorted = [&](int32_t at, int32_t total, int32_t used) -> bool {
+            if (a.mode == kStage && out + total > q4) {
+              // staged pairs would not fit the scratch (sized by wedges +
+              // core items): report instead of writing past it
+              if (threadIdx.x == 0) raise_error(meta, SLG_ERR_INVALID, kWhereGiant);
+              table_reset_front<kGiantNT>(tab, used);
+              return false;
+            }
+            if (emit && total > 0) {
+              for (int32_t i = threadIdx.x; i < total; i += kGiantNT) {
+                const unsigned long long x = tab[at + i];
+                const int32_t f = (int32_t)(x >> 32), n = (int32_t)(uint32_t)x;
+                if (a.mode == kDirect) {
+                  put(a, base, out + i, e, f, n);
+                } else {
+                  tj[out + i] = f;
+                  if (!unweighted) tw[out + i] = n;
+                }
               }
             }
+            out += total;
+            table_reset_front<kGiantNT>(tab, used);
+            return true;
+          };
+          // sub-ranges [h0, h1) (wedges wl[hlo, hhi), tile items `hnit`)
+          // counted in the hash table
+          auto hash_bucket = [&](int32_t h0, int32_t h1, int32_t hlo, int32_t hhi,
+                                 int32_t hnit) -> bool {
+            const int32_t width = (h1 - h0) << shift;
+            const int lgT = table_lg(min(hhi - hlo + hnit, width), lg_max);
+            const int32_t T = 1 << lgT;
+            // s >= 2: survivors listed as they appear; s = 1: every key survives
+            const bool list = smin >= 2;
+            auto insert_all = [&](auto list_tag) {
+              constexpr bool L = decltype(list_tag)::value;
+              for_each_batched<kGiantNT, 8>(wl, hlo, hhi, [&](int32_t f) {
+                table_insert<L>(tab, lgT, f, 1, smin, unweighted, meta, sl);
+              });
+              if (core_row && hnit > 0)
+                for (int32_t p = s_misc[2] + (int32_t)threadIdx.x; p < s_misc[3];
+                     p += kGiantNT) {
+                  const int32_t f = ci.core_list[p];
+                  const int32_t wt = Trow[p];
+                  if (wt > 0 && w.r_off[f + 1] - w.r_off[f] >= smin)
+                    table_insert<L>(tab, lgT, f, wt, smin, unweighted, meta, sl);
+                }
+            };
+            int32_t at = 0, used = T, total;
+            if (list) {
+              insert_all(std::true_type{});
+              total = table_collect_list<kGiantNT, kGiantQ>(tab, T, sl, emit, &at, &used);
+            } else {
+              insert_all(std::false_type{});
+              __syncthreads();
+              total = table_collect<kGiantNT, kGiantSPT>(tab, T, smin, emit, ws, &at, &used);
+            }
+            return emit_sorted(at, total, used);
+          };
+          if (bloom_row) {
+            // two passes over the bucket's far ends: Bloom filter (in the
+            // survivor-list area) and candidates (table slots [0, kSpT),
+            // candidate filter in the tile-item area), then exact counts of
+            // the candidates
+            uint32_t *filt = reinterpret_cast<uint32_t *>(sl.slot);
+            uint32_t *cand = reinterpret_cast<uint32_t *>(subt);
+            {
+              uint4 *f4 = reinterpret_cast<uint4 *>(filt);
+              for (int i = threadIdx.x; i < (1 << (kGiantLogB - 7)); i += kGiantNT)
+                f4[i] = make_uint4(0, 0, 0, 0);
+              for (int i = threadIdx.x; i < (1 << (kGiantLogB - 7)); i += kGiantNT) cand[i] = 0u;
+              if (threadIdx.x == 0) s_x[0] = 0;
+            }
+            __syncthreads();
+            for_each_batched<kGiantNT, 8>(wl, lo, hi, [&](int32_t f) {
+              const uint32_t h = sp_h1(f, kGiantLogB), m = 1u << (h & 31);
+              if (atomicOr(filt + (h >> 5), m) & m)
+                sp_candidate(tab, cand, f, s_x, kGiantLogB, kSpLgT);
+            });
+            __syncthreads();
+            int32_t at = 0, used = kSpT, total = -1;
+            if (!s_x[0]) {  // uniform
+              for_each_batched<kGiantNT, 8>(wl, lo, hi, [&](int32_t f) {
+                sp_count(tab, cand, f, smin, unweighted, kGiantLogB, kSpLgT);
+              });
+              __syncthreads();
+              total = table_collect<kGiantNT, kGiantSPT, true>(tab, kSpT, smin, emit, ws, &at,
+                                                               &used, (kSpT - 32) / 2);
+            }
+            if (total >= 0) {
+              if (!emit_sorted(at, total, used)) break;
+              continue;
+            }
+            // too many candidates: the hash table counts the bucket in
+            // sub-buckets of at most cap_hash wedges (or one sub-range)
+            __syncthreads();
+            for (int i = threadIdx.x; i < kSpT; i += kGiantNT) tab[i] = kEmpty64;
+            bool ok = true;
+            for (int32_t h0 = b0; h0 < b1;) {
+              __syncthreads();  // s_x[1] of the previous sub-bucket read
+              if (threadIdx.x == 0) {
+                int32_t h1 = h0 + 1;
+                const int32_t start = h0 ? sub[h0 - 1] : 0;
+                while (h1 < b1 && sub[h1] - start <= cap_hash) ++h1;
+                s_x[1] = h1;
+              }
+              __syncthreads();
+              const int32_t h1 = s_x[1];
+              ok = hash_bucket(h0, h1, h0 ? sub[h0 - 1] : 0, sub[h1 - 1], 0);
+              if (!ok) break;
+              h0 = h1;
+            }
+            if (!ok) break;
+            continue;
           }
-          out += total;
-          table_reset_front<kGiantNT>(tab, used);
+          if (!hash_bucket(b0, b1, lo, hi, nit)) break;
         }
         clk_bucket += clock64() - c1;
       }
@@ -969,137 +1184,6 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
           if (!unweighted) a.stage_w[b + i] = tw[i];
         }
     }
-  }
-}
-
-// ------------------------------------------------------------ sparse bin --
-//
-// Large rows whose far ends are sparse in their id span, with s >= 2.  Almost
-// every far end of such a row occurs once (on the Chung-Lu workloads about
-// 96 % of the wedges of these rows are the only wedge to their far end), and
-// a far end with a single wedge can never reach s >= 2.  The row is counted
-// in two walks with little shared memory, so that several rows are in
-// flight on each SM (the walk's far-end gathers are latency-bound: a row at
-// a time per SM leaves the memory system idle):
-//   1. every wedge sets its far end's bit in a one-hash Bloom filter (one
-//      shared atomicOr); a wedge that finds the bit already set makes f a
-//      candidate: f is claimed in a small shared table (key, count 0) and
-//      marked in a second filter.  Every f with two or more wedges becomes
-//      a candidate (its second wedge finds the bit set); so may a few
-//      single-wedge f whose bit another f had set;
-//   2. a second walk counts, exactly, every wedge whose far end is a
-//      candidate (the second filter screens out almost all others before
-//      the table is probed).  The count of f is then |e ∩ f|.
-// The candidates with count >= s are sorted and emitted.  A row of at most
-// kSpCache wedges keeps its far ends in shared memory during the first walk
-// and reads them from there in the second.  A row whose candidates overflow
-// the table (a probe sequence longer than kSpMaxProbe) is handed to the
-// giant bin, which runs after this one.
-
-#ifndef SLG_SP_NT
-#define SLG_SP_NT 256
-#endif
-#ifndef SLG_SP_LOGB
-#define SLG_SP_LOGB 17
-#endif
-#ifndef SLG_SP_LGT
-#define SLG_SP_LGT 12
-#endif
-#ifndef SLG_SP_CACHE
-#define SLG_SP_CACHE 0
-#endif
-#ifndef SLG_SP_MINB
-#define SLG_SP_MINB 4
-#endif
-#ifndef SLG_SP_G
-#define SLG_SP_G 6
-#endif
-#ifndef SLG_SP_RUNS
-#define SLG_SP_RUNS 1  // order survivor sets above 64 by sorted warp runs
-#endif
-constexpr int kSpNT = SLG_SP_NT;
-constexpr int kSpLogB = SLG_SP_LOGB;          // Bloom filter bits (log2)
-constexpr int kSpWords = 1 << (kSpLogB - 5);
-constexpr int kSpCWords = kSpWords / 4;       // candidate filter words
-constexpr int kSpLgT = SLG_SP_LGT;
-constexpr int kSpT = 1 << kSpLgT;             // candidate table slots
-constexpr int kSpCache = SLG_SP_CACHE;        // far ends kept of a small row
-constexpr int kSpMaxProbe = 32;
-constexpr int kSpG = SLG_SP_G;                // wedges per thread per walk step
-constexpr int kSpSPT = kSpT / kSpNT;          // table slots per thread
-static_assert(kSpSPT >= 1 && kSpWords % (4 * kSpNT) == 0 && kSpCWords % 4 == 0,
-              "sparse bin geometry");
-
-// [s_base 8][s_ovf 4][s_row 4][pad 16][filter kSpWords x 4]
-// [candidate filter kSpCWords x 4][table kSpT x 8][cache kSpCache x 4]
-// [s_beg NT][s_pref NT+1][ws NT/32+1]
-constexpr size_t sparse_smem() {
-  return 32 + (size_t)kSpWords * 4 + (size_t)kSpCWords * 4 + (size_t)kSpT * 8 +
-         (size_t)kSpCache * 4 + (size_t)(2 * kSpNT + 1 + kSpNT / 32 + 1) * 4;
-}
-
-// A row's filter has 2^lgb bits (its candidate filter 2^(lgb - 2)) and its
-// table 2^lgt slots, sized by the row's work (see sp_sizes).
-__device__ __forceinline__ uint32_t sp_h1(int32_t f, int lgb) {  // Bloom filter bit
-  return ((uint32_t)f * 0x9E3779B1u) >> (32 - lgb);
-}
-__device__ __forceinline__ uint32_t sp_h2(int32_t f, int lgb) {  // candidate filter bit
-  return ((uint32_t)f * 0x85EBCA6Bu) >> (34 - lgb);
-}
-__device__ __forceinline__ uint32_t sp_ht(int32_t f, int lgt) {  // candidate table slot
-  return ((uint32_t)f * 0xC2B2AE35u) >> (32 - lgt);
-}
-
-// Per-row sizes: a filter of >= 32 bits per wedge (so that a single-wedge
-// far end finds its bit set by another with probability below 1/64 on
-// average) and a table of >= one slot per wedge (every candidate has two
-// wedges or is such a collision), within the shared-memory maxima.
-__device__ __forceinline__ void sp_sizes(int32_t work, int *lgb, int *lgt) {
-  const int lw = ceil_log2(work > 1 ? work : 2);
-  *lgb = min(max(lw + 5, 12), kSpLogB);
-  *lgt = min(max(lw, 7), kSpLgT);
-}
-
-// Pass 1: f is a candidate (its filter bit was already set).  Claims f's
-// table slot (32-bit CAS on the key word; the count word stays 0) unless it
-// is there already, and marks it in the candidate filter.  A probe sequence
-// longer than kSpMaxProbe marks the row as overflowed.
-__device__ __forceinline__ void sp_candidate(unsigned long long *tab, uint32_t *cand, int32_t f,
-                                             int32_t *s_ovf, int lgb, int lgt) {
-  if (*(volatile int32_t *)s_ovf) return;
-  const uint32_t mask = (1u << lgt) - 1u;
-  uint32_t h = sp_ht(f, lgt);
-  for (int probe = 0; probe < kSpMaxProbe; ++probe) {
-    const uint32_t k = atomicCAS(count_word(tab, h) + 1, 0xFFFFFFFFu, (uint32_t)f);
-    if (k == 0xFFFFFFFFu) {
-      const uint32_t c = sp_h2(f, lgb);
-      atomicOr(cand + (c >> 5), 1u << (c & 31));
-      return;
-    }
-    if (k == (uint32_t)f) return;
-    h = (h + 1) & mask;
-  }
-  *(volatile int32_t *)s_ovf = 1;
-}
-
-// Pass 2: one wedge to f; counted when f is a candidate.  Unweighted: a
-// count that reached s is not raised further.
-__device__ __forceinline__ void sp_count(unsigned long long *tab, const uint32_t *cand,
-                                         int32_t f, int32_t smin, bool unweighted, int lgb,
-                                         int lgt) {
-  const uint32_t c = sp_h2(f, lgb);
-  if (!(cand[c >> 5] & (1u << (c & 31)))) return;
-  const uint32_t mask = (1u << lgt) - 1u;
-  uint32_t h = sp_ht(f, lgt);
-  for (int probe = 0; probe < kSpMaxProbe; ++probe) {
-    uint32_t *cw = count_word(tab, h);
-    const uint32_t k = cw[1];
-    if (k == (uint32_t)f) {
-      if (!unweighted || (int32_t)*(volatile uint32_t *)cw < smin) atomicAdd(cw, 1u);
-      return;
-    }
-    if (k == 0xFFFFFFFFu) return;
-    h = (h + 1) & mask;
   }
 }
 

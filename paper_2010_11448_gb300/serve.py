@@ -35,8 +35,8 @@ import time
 
 import numpy as np
 
-from . import (DeviceHypergraph, SlgError, alloc_outputs, build, filter_pairs, last_stats,
-               wedges)
+from . import (DeviceHypergraph, SlgError, alloc_outputs, build, count, filter_pairs,
+               last_stats, release_memory, wedges)
 
 _FIRST_GUESS = 1 << 24  # pairs, when nothing bounds a query's list yet
 
@@ -66,12 +66,23 @@ class Query:
         return (self.t_done - self.t_submit) * 1e3
 
 
+class ResultTooLarge(RuntimeError):
+    """The query's list is larger than the server's per-query limit."""
+
+
 class Server:
-    """Continuous-batching scheduler over a resident pool of hypergraphs."""
+    """Continuous-batching scheduler over a resident pool of hypergraphs.
+
+    A query whose list would take more than ``max_result_bytes`` (20 bytes a
+    pair: the (i, j, w) output and the build's staging) is refused with
+    ResultTooLarge; for s = 1, whose lists can be far larger than any other
+    threshold's, the size is counted (one walk, no output) before the build.
+    """
 
     def __init__(self, graphs: list[DeviceHypergraph], slots: int = 4,
                  memory_budget: int = 64 << 30, keep_results: bool = False,
-                 reuse: bool = False, cache_bytes: int = 32 << 30, base_s: int | None = 2):
+                 reuse: bool = False, cache_bytes: int = 32 << 30, base_s: int | None = 2,
+                 max_result_bytes: int | None = None):
         import torch
         self.graphs = graphs
         self.keep = keep_results
@@ -82,6 +93,8 @@ class Server:
         self.building = {}   # (gid, dual) -> threading.Event while its base list is built
         self.cache_used = 0
         self.budget = int(memory_budget)
+        self.max_result = int(max_result_bytes if max_result_bytes is not None
+                              else memory_budget // 2)
         self.in_flight = 0
         self.pending = collections.deque()
         self.cv = threading.Condition()
@@ -197,6 +210,13 @@ class Server:
         guess of its size was too small)."""
         g = self.graphs[q.gid]
         n = self._bound(q.gid, q.dual, s)
+        if n is None and s == 1:
+            q.walks += 1
+            n = count(g, s, q.dual, stream=st)
+            self._known(q.gid, q.dual, s, n)
+            self._resize(q, n)
+        if n is not None and s == 1 and 20 * n > self.max_result:
+            raise ResultTooLarge(f"L_1 of graph {q.gid}{'*' if q.dual else ''} has {n} pairs")
         cap = n if n is not None else _FIRST_GUESS
         for attempt in (0, 1):
             out = alloc_outputs(max(cap, 1), False, g.e_off.device)
@@ -211,6 +231,19 @@ class Server:
                 cap = exc.needed            # the exact size, counted by the walk
                 self._known(q.gid, q.dual, s, cap)
                 del out
+                self._resize(q, cap)
+                if 20 * cap > self.max_result:
+                    raise ResultTooLarge(f"L_{s} of graph {q.gid}{'*' if q.dual else ''} has "
+                                         f"{cap} pairs") from None
+
+    def _resize(self, q: Query, pairs: int):
+        """The query's list turned out to have `pairs` pairs: its share of
+        the memory budget follows (new queries see it at admission)."""
+        nnz, rows, cols, maxw = self.shape[(q.gid, q.dual)]
+        est = 4 * (7 * nnz + 12 * rows + cols) + 304 * 16 * maxw + 20 * pairs
+        with self.cv:
+            self.in_flight += est - q.est_bytes
+            q.est_bytes = est
 
     def _base_list(self, q: Query, st):
         """The kept base list of the query's graph and side, built now if it
@@ -279,13 +312,16 @@ class Server:
                         st.synchronize()
                         break
                     except (SlgError, torch.cuda.OutOfMemoryError) as exc:
-                        # out of device memory: give the kept lists back, retry once
-                        if attempt or getattr(exc, "status", 3) != 3 or not self.reuse:
+                        # out of device memory: give the kept lists and both
+                        # allocators' cached memory back, retry once
+                        if attempt or getattr(exc, "status", 3) != 3:
                             raise
-                        with self.cv:
-                            self.cached.clear()
-                            self.cache_used = 0
+                        if self.reuse:
+                            with self.cv:
+                                self.cached.clear()
+                                self.cache_used = 0
                         torch.cuda.empty_cache()
+                        release_memory()
                 q.pairs = int(i.shape[0])
                 if self.keep:
                     q.result = (i, j, w)
@@ -306,6 +342,7 @@ class Server:
         return {"queries": len(queries), "errors": len(errs),
                 "first_error": (f"{errs[0].gid}/{errs[0].s}/{errs[0].dual}: {errs[0].error!r}"
                                 if errs else None),
+                "too_large": sum(isinstance(q.error, ResultTooLarge) for q in queries),
                 "answered_by_filter": sum(q.reused for q in queries),
                 "walks": sum(q.walks for q in queries),
                 "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
