@@ -662,7 +662,7 @@ def run_serve(args):
     import numpy as np
     # lists of very different sizes come and go: let torch's allocator grow
     # and shrink its segments instead of keeping fragments
-    os.environ.setdefault("PYTORCH_CUDA_ALLOC_CONF", "expandable_segments:True")
+    os.environ.setdefault("PYTORCH_ALLOC_CONF", "expandable_segments:True")
     torch, slg = _setup_gpu()
     import hypergen
     from paper_2010_11448_gb300.serve import Server
@@ -677,9 +677,11 @@ def run_serve(args):
     qs_spec = [(int(rng.integers(0, 16)), int(rng.integers(1, 65)), bool(rng.integers(0, 2)))
                for _ in range(n)]
     runs = {}
-    for reuse in (False, True):
+    for name, reuse, warm in (("walk_every_query", False, False), ("base_lists", True, False),
+                              ("base_lists_warm", True, True)):
         srv = Server(dhs, slots=4, memory_budget=96 << 30, reuse=reuse, cache_bytes=48 << 30,
                      base_s=2)
+        warm_s = srv.warm() if warm else 0.0
         t0 = time.perf_counter()
         due = t0
         queries = []
@@ -694,7 +696,9 @@ def run_serve(args):
         wall = time.perf_counter() - t0
         srv.close()
         slg.release_memory()
-        runs["base_lists" if reuse else "walk_every_query"] = Server.summary(queries, wall)
+        runs[name] = Server.summary(queries, wall)
+        if warm:
+            runs[name]["warm_s"] = warm_s
         del srv, queries
         torch.cuda.empty_cache()
     torch.cuda.empty_cache()

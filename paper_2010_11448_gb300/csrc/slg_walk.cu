@@ -712,15 +712,6 @@ constexpr int kGiantG = 6;  // wedges per thread per step of the giant bin's wal
 static_assert(kGiantDirectMax <= kGiantTMax && kGiantDirectMax / 2 <= kGiantList,
               "a direct row fits the table and the survivor list");
 constexpr int kGiantQ = kGiantList / kGiantNT;
-// Bloom-counted buckets (s >= 2, sparse rows): at most this many wedges; the
-// filter takes the survivor-list area (2^kGiantLogB bits).
-#ifndef SLG_GIANT_BLOOM_CAP
-#define SLG_GIANT_BLOOM_CAP 12288
-#endif
-constexpr int32_t kGiantBloomCap = SLG_GIANT_BLOOM_CAP;
-constexpr int kGiantLogB = 17;
-static_assert((1 << (kGiantLogB - 3)) <= kGiantList * 4, "the filter fits the list area");
-static_assert((1 << (kGiantLogB - 7)) <= kNSB, "the candidate filter fits the item area");
 
 // [s_base 16][s_misc 16][table TMAX x 8][sub NSB][subt NSB+1][bstart NSB+1]
 // [s_beg NT][s_pref NT+1][ws NT/32+1][list kGiantList][list count 1]
@@ -789,7 +780,6 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
   if (meta->err) return;
   extern __shared__ __align__(16) unsigned char smem[];
   long long *s_base = reinterpret_cast<long long *>(smem);
-  int32_t *s_x = reinterpret_cast<int32_t *>(smem + 8);      // [0] overflow, [1] boundary
   int32_t *s_misc = reinterpret_cast<int32_t *>(smem + 16);  // [0] row, [1] buckets, [2,3] items
   unsigned long long *tab = reinterpret_cast<unsigned long long *>(smem + 32);
   int32_t *sub = reinterpret_cast<int32_t *>(tab + kGiantTMax);
@@ -831,7 +821,7 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
     const int32_t span = f_hi - f_lo;
     const int shift = min(kShiftMax, max(0, ceil_log2(span) - kNSBLog));
     const int32_t chunk_w = kNSB << shift;  // ids per super-chunk
-    const int32_t cap_hash = kGiantTMax / 2 - (1 << shift);
+    const int32_t cap = kGiantTMax / 2 - (1 << shift);
     const int32_t work = a.row_work[e - a.row_begin];
     // Dense rows (at least one wedge per 8 ids) count fixed windows of
     // kDenseW ids in a dense shared array: no hashing, no sort.
@@ -844,11 +834,6 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
     // core row f > e with a non-zero tile count.
     const CoreInfo &ci = a.core;
     const bool core_row = ci.T && ci.row_rank[e + 1] != ci.row_rank[e];
-    // Sparse buckets with s >= 2 are counted in two passes with a Bloom
-    // filter (as the sparse bin counts rows), so they can hold kGiantBloomCap
-    // wedges instead of what a table of their distinct far ends allows.
-    const bool bloom_row = smin >= 2 && !dense && !core_row;
-    const int32_t cap = bloom_row ? kGiantBloomCap : cap_hash;
     const int32_t ri = core_row ? ci.row_rank[e] : 0;
     const int32_t *Trow = core_row ? ci.T + (long long)ri * ci.Mp : nullptr;
     long long base = -1;
@@ -1109,62 +1094,6 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
             }
             return emit_sorted(at, total, used);
           };
-          if (bloom_row) {
-            // two passes over the bucket's far ends: Bloom filter (in the
-            // survivor-list area) and candidates (table slots [0, kSpT),
-            // candidate filter in the tile-item area), then exact counts of
-            // the candidates
-            uint32_t *filt = reinterpret_cast<uint32_t *>(sl.slot);
-            uint32_t *cand = reinterpret_cast<uint32_t *>(subt);
-            {
-              uint4 *f4 = reinterpret_cast<uint4 *>(filt);
-              for (int i = threadIdx.x; i < (1 << (kGiantLogB - 7)); i += kGiantNT)
-                f4[i] = make_uint4(0, 0, 0, 0);
-              for (int i = threadIdx.x; i < (1 << (kGiantLogB - 7)); i += kGiantNT) cand[i] = 0u;
-              if (threadIdx.x == 0) s_x[0] = 0;
-            }
-            __syncthreads();
-            for_each_batched<kGiantNT, 8>(wl, lo, hi, [&](int32_t f) {
-              const uint32_t h = sp_h1(f, kGiantLogB), m = 1u << (h & 31);
-              if (atomicOr(filt + (h >> 5), m) & m)
-                sp_candidate(tab, cand, f, s_x, kGiantLogB, kSpLgT);
-            });
-            __syncthreads();
-            int32_t at = 0, used = kSpT, total = -1;
-            if (!s_x[0]) {  // uniform
-              for_each_batched<kGiantNT, 8>(wl, lo, hi, [&](int32_t f) {
-                sp_count(tab, cand, f, smin, unweighted, kGiantLogB, kSpLgT);
-              });
-              __syncthreads();
-              total = table_collect<kGiantNT, kGiantSPT, true>(tab, kSpT, smin, emit, ws, &at,
-                                                               &used, (kSpT - 32) / 2);
-            }
-            if (total >= 0) {
-              if (!emit_sorted(at, total, used)) break;
-              continue;
-            }
-            // too many candidates: the hash table counts the bucket in
-            // sub-buckets of at most cap_hash wedges (or one sub-range)
-            __syncthreads();
-            for (int i = threadIdx.x; i < kSpT; i += kGiantNT) tab[i] = kEmpty64;
-            bool ok = true;
-            for (int32_t h0 = b0; h0 < b1;) {
-              __syncthreads();  // s_x[1] of the previous sub-bucket read
-              if (threadIdx.x == 0) {
-                int32_t h1 = h0 + 1;
-                const int32_t start = h0 ? sub[h0 - 1] : 0;
-                while (h1 < b1 && sub[h1] - start <= cap_hash) ++h1;
-                s_x[1] = h1;
-              }
-              __syncthreads();
-              const int32_t h1 = s_x[1];
-              ok = hash_bucket(h0, h1, h0 ? sub[h0 - 1] : 0, sub[h1 - 1], 0);
-              if (!ok) break;
-              h0 = h1;
-            }
-            if (!ok) break;
-            continue;
-          }
           if (!hash_bucket(b0, b1, lo, hi, nit)) break;
         }
         clk_bucket += clock64() - c1;

@@ -39,6 +39,8 @@ from . import (DeviceHypergraph, SlgError, alloc_outputs, build, count, filter_p
                last_stats, release_memory, wedges)
 
 _FIRST_GUESS = 1 << 24  # pairs, when nothing bounds a query's list yet
+_GUESS_DIV = 16         # ... or W_s / 16: a pair of L_s takes >= s >= 2 of its wedges,
+                        # and on these workloads about 1 wedge in 20 ends in a pair
 
 
 class Query:
@@ -174,6 +176,26 @@ class Server:
             return True
 
     # ----------------------------------------------------------------- API --
+    def warm(self) -> float:
+        """Builds and keeps the base list of every graph and side now (reuse
+        with base_s set), so that queries with s >= base_s are answered by
+        filters from their first arrival.  Returns the seconds it took."""
+        import torch
+        if not self.reuse or self.base_s is None:
+            return 0.0
+        t0 = time.perf_counter()
+        st = self.streams[0]
+        for gid in range(len(self.graphs)):
+            for dual in (False, True):
+                q = Query(gid, self.base_s, dual)
+                try:
+                    with torch.cuda.stream(st):
+                        self._base_list(q, st)
+                except (SlgError, ResultTooLarge, torch.cuda.OutOfMemoryError):
+                    pass  # not kept: such queries walk
+        st.synchronize()
+        return time.perf_counter() - t0
+
     def submit(self, gid: int, s: int, dual: bool = False) -> Query:
         q = Query(gid, s, dual)
         q.t_submit = time.perf_counter()
@@ -217,7 +239,10 @@ class Server:
             self._resize(q, n)
         if n is not None and s == 1 and 20 * n > self.max_result:
             raise ResultTooLarge(f"L_1 of graph {q.gid}{'*' if q.dual else ''} has {n} pairs")
-        cap = n if n is not None else _FIRST_GUESS
+        if n is None:  # first guess: from W_s (slg_wedges: planning only, no walk)
+            guess = wedges(g, s, q.dual, stream=st) // _GUESS_DIV
+            n = min(max(guess, 1 << 16), self.max_result // 20)
+        cap = n
         for attempt in (0, 1):
             out = alloc_outputs(max(cap, 1), False, g.e_off.device)
             q.walks += 1
