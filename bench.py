@@ -680,7 +680,7 @@ def run_serve(args):
     for name, reuse, warm in (("walk_every_query", False, False), ("base_lists", True, False),
                               ("base_lists_warm", True, True)):
         srv = Server(dhs, slots=4, memory_budget=96 << 30, reuse=reuse, cache_bytes=48 << 30,
-                     base_s=2)
+                     base_s=2, max_result_bytes=48 << 30)
         warm_s = srv.warm() if warm else 0.0
         t0 = time.perf_counter()
         due = t0
@@ -692,7 +692,8 @@ def run_serve(args):
                 time.sleep(due - now)
             queries.append(srv.submit(*spec))
         for q in queries:
-            q.wait()
+            if not q.wait(900):
+                raise RuntimeError(f"serving: query {q.gid}/{q.s}/{q.dual} did not complete")
         wall = time.perf_counter() - t0
         srv.close()
         slg.release_memory()

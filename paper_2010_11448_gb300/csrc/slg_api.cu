@@ -259,20 +259,27 @@ struct Call {
   int32_t launches;
   int64_t core_rows, core_cols, core_nnz;
   Meta *meta_host;  // this host thread's pinned copy of the device Meta
+  Meta *meta_view;  // the same memory as the device addresses it
 };
 
 // One pinned Meta per host thread (calls on different threads and streams
 // run concurrently; each reads its own results).
-cudaError_t thread_meta(Meta **out) {
-  thread_local Meta *m = nullptr;
+// This host thread's copy of the device Meta: pinned and mapped, so that a
+// kernel writes it (read_meta) without the copy engines, which may be busy
+// with large copies of other work (the results of slg_build_host_many).
+cudaError_t thread_meta(Meta **out, Meta **view = nullptr) {
+  thread_local Meta *m = nullptr, *v = nullptr;
   if (!m) {
-    cudaError_t e = cudaMallocHost(&m, sizeof(Meta));
+    cudaError_t e = cudaHostAlloc(&m, sizeof(Meta), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&v), m, 0);
     if (e != cudaSuccess) {
-      m = nullptr;
+      if (m) cudaFreeHost(m);
+      m = v = nullptr;
       return e;
     }
   }
   *out = m;
+  if (view) *view = v;
   return cudaSuccess;
 }
 
@@ -307,7 +314,7 @@ cudaError_t giant_scratch(Call &c, int32_t max_work, WalkLaunch *L) {
 thread_local int32_t t_err_where = 0;  // kWhere* of the last device-raised error
 
 int read_meta(Call &c) {
-  SLG_TRY(cudaMemcpyAsync(c.meta_host, c.w.meta, sizeof(Meta), cudaMemcpyDeviceToHost, c.st));
+  SLG_TRY(launch_meta_copy(c.w.meta, c.meta_view, c.st));
   SLG_TRY(cudaStreamSynchronize(c.st));
   if (c.meta_host->err) t_err_where = c.meta_host->err_where;
   return c.meta_host->err;
@@ -718,7 +725,7 @@ int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin
 
   int dev = 0;
   DeviceCtx &ctx = ctx_for_current(&dev);
-  SLG_TRY(thread_meta(&c.meta_host));
+  SLG_TRY(thread_meta(&c.meta_host, &c.meta_view));
   c.ctx = &ctx;
 
   Events evs(t_profile != 0 && op != kOpWedges);

@@ -112,7 +112,19 @@ __global__ __launch_bounds__(kNT) void k_gather(int32_t row_begin, int32_t rows,
   }
 }
 
+__global__ void k_meta_copy(const uint32_t *__restrict__ src, volatile uint32_t *dst, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
 }  // namespace
+
+cudaError_t launch_meta_copy(const Meta *src, Meta *dst, cudaStream_t st) {
+  static_assert(sizeof(Meta) % 4 == 0, "Meta is copied as 32-bit words");
+  k_meta_copy<<<1, 128, 0, st>>>(reinterpret_cast<const uint32_t *>(src),
+                                 reinterpret_cast<volatile uint32_t *>(dst),
+                                 (int)(sizeof(Meta) / 4));
+  return cudaGetLastError();
+}
 
 cudaError_t launch_row_scan(int32_t rows, const Work &w, cudaStream_t st) {
   const int32_t ntiles = (rows + kTile - 1) / kTile;

@@ -475,6 +475,9 @@ constexpr int kWalkEv[kNumBins] = {0, 1, 2, 4, 3};
 cudaError_t launch_walk(const WalkLaunch &L, cudaStream_t st, int32_t *launches,
                         cudaEvent_t *ev = nullptr);
 cudaError_t launch_row_scan(int32_t rows, const Work &w, cudaStream_t st);
+// The device Meta into host memory the device can address (mapped pinned
+// memory), by a kernel: no copy engine involved.
+cudaError_t launch_meta_copy(const Meta *src, Meta *dst, cudaStream_t st);
 // out_cap: entries of the output arrays (a row beyond them raises an error).
 cudaError_t launch_gather(int32_t row_begin, int32_t rows, const Work &w, int32_t *out_i,
                           int32_t *out_j, int32_t *out_w, int unweighted, long long out_cap,

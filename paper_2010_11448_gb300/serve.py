@@ -47,7 +47,7 @@ class Query:
     """One request and its outcome."""
 
     __slots__ = ("gid", "s", "dual", "t_submit", "t_start", "t_done", "pairs", "result",
-                 "error", "est_bytes", "reused", "walks", "_done")
+                 "error", "est_bytes", "admitted", "reused", "walks", "_done")
 
     def __init__(self, gid: int, s: int, dual: bool):
         self.gid, self.s, self.dual = gid, s, dual
@@ -56,6 +56,7 @@ class Query:
         self.result = None
         self.error = None
         self.est_bytes = 0
+        self.admitted = False   # counted in the server's memory in flight
         self.reused = False
         self.walks = 0
         self._done = threading.Event()
@@ -75,10 +76,11 @@ class ResultTooLarge(RuntimeError):
 class Server:
     """Continuous-batching scheduler over a resident pool of hypergraphs.
 
-    A query whose list would take more than ``max_result_bytes`` (20 bytes a
-    pair: the (i, j, w) output and the build's staging) is refused with
-    ResultTooLarge; for s = 1, whose lists can be far larger than any other
-    threshold's, the size is counted (one walk, no output) before the build.
+    With ``max_result_bytes`` set, a query whose list would take more than
+    that (20 bytes a pair: the (i, j, w) output and the build's staging) is
+    refused with ResultTooLarge; for s = 1, whose lists can be far larger
+    than any other threshold's, the size is counted (one walk, no output)
+    before the build.
     """
 
     def __init__(self, graphs: list[DeviceHypergraph], slots: int = 4,
@@ -95,9 +97,9 @@ class Server:
         self.building = {}   # (gid, dual) -> threading.Event while its base list is built
         self.cache_used = 0
         self.budget = int(memory_budget)
-        self.max_result = int(max_result_bytes if max_result_bytes is not None
-                              else memory_budget // 2)
-        self.in_flight = 0
+        self.max_result = int(max_result_bytes) if max_result_bytes is not None else 1 << 62
+        self.in_flight = 0     # estimated bytes of the admitted queries
+        self.n_in_flight = 0   # admitted queries not yet done
         self.pending = collections.deque()
         self.cv = threading.Condition()
         self.closed = False
@@ -218,10 +220,12 @@ class Server:
                 for k, q in enumerate(self.pending):
                     est = self._estimate(q)
                     # the oldest query that fits; a lone query is always admitted
-                    if self.in_flight == 0 or self.in_flight + est <= self.budget:
+                    if self.n_in_flight == 0 or self.in_flight + est <= self.budget:
                         del self.pending[k]
                         q.est_bytes = est
+                        q.admitted = True
                         self.in_flight += est
+                        self.n_in_flight += 1
                         return q
                 if self.closed and not self.pending:
                     return None
@@ -264,6 +268,8 @@ class Server:
     def _resize(self, q: Query, pairs: int):
         """The query's list turned out to have `pairs` pairs: its share of
         the memory budget follows (new queries see it at admission)."""
+        if not q.admitted:  # a warm-up build outside the admission count
+            return
         nnz, rows, cols, maxw = self.shape[(q.gid, q.dual)]
         est = 4 * (7 * nnz + 12 * rows + cols) + 304 * 16 * maxw + 20 * pairs
         with self.cv:
@@ -355,6 +361,8 @@ class Server:
             q.t_done = time.perf_counter()
             with self.cv:
                 self.in_flight -= q.est_bytes
+                self.n_in_flight -= 1
+                q.admitted = False
                 self.done.append(q)
                 self.cv.notify_all()
             q._done.set()

@@ -112,3 +112,22 @@ def test_eager_base_lists_equal_walks(pool):
     # one base build per graph and side (two walks at most when the first
     # size guess was short), one walk per s = 1 query (two at most)
     assert st["walks"] <= 2 * (len(keys) + ones)
+
+
+def test_warm_start_then_stream(pool):
+    # warm() builds every base list before the queries arrive; afterwards the
+    # memory in flight is back to zero and every s >= 2 query is a filter
+    from paper_2010_11448_gb300.serve import Server
+    hs, dhs = pool
+    srv = Server(dhs, slots=3, keep_results=True, reuse=True, base_s=2, memory_budget=1 << 30)
+    assert srv.warm() > 0
+    assert srv.in_flight == 0 and len(srv.cached) == 2 * len(dhs)
+    reqs = [(g, s, d) for g in range(len(dhs)) for s in (1, 2, 7) for d in (False, True)]
+    qs = [srv.submit(*r) for r in reqs]
+    for q in qs:
+        assert q.wait(300)
+    srv.close()
+    assert srv.in_flight == 0
+    for (gid, s, dual), q in zip(reqs, qs):
+        assert q.error is None and q.reused == (s >= 2)
+        assert np.array_equal(as_np(q.result), as_np(slg.build(dhs[gid], s, dual=dual)))
