@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define SLG_ABI_VERSION 5
+#define SLG_ABI_VERSION 6
 
 /* Incidence of H as CSR + CSC (Section III: the hyperedge/vertex incidence
  * and its bipartite form).  All pointers are device pointers. */
@@ -470,8 +470,10 @@ typedef struct slg_stats {
   int64_t core_rows;       /* dense core used by SLG_TENSOR_CORE: rows, */
   int64_t core_cols;       /* columns and incidences (0 when no core was */
   int64_t core_nnz;        /* found or the flag was not given) */
-  int64_t giant_cycles[3]; /* giant bin, SM clock cycles summed over CTAs:
-                              walk, partition into buckets, bucket counting */
+  int64_t giant_cycles[4]; /* giant bin, SM clock cycles summed over CTAs:
+                              walk, partition into buckets, bucket counting
+                              (of partitioned rows), and the whole of its
+                              dense rows */
   int64_t max_row_work;    /* largest wedge count of one row */
   float ms_relabel;        /* SLG_RELABEL_*: building the renumbered side */
   float ms_order;          /* SLG_RELABEL_*: caller ids and (i, j) order */

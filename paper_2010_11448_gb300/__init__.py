@@ -85,7 +85,7 @@ class _Stats(ctypes.Structure):
                 ("core_rows", ctypes.c_int64),
                 ("core_cols", ctypes.c_int64),
                 ("core_nnz", ctypes.c_int64),
-                ("giant_cycles", ctypes.c_int64 * 3),
+                ("giant_cycles", ctypes.c_int64 * 4),
                 ("max_row_work", ctypes.c_int64),
                 ("ms_relabel", ctypes.c_float),
                 ("ms_order", ctypes.c_float),

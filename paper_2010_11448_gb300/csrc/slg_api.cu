@@ -824,7 +824,7 @@ int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin
   stats.core_rows = c.core_rows;
   stats.core_cols = c.core_cols;
   stats.core_nnz = c.core_nnz;
-  for (int q = 0; q < 3; ++q) stats.giant_cycles[q] = (int64_t)m.giant_cycles[q];
+  for (int q = 0; q < 4; ++q) stats.giant_cycles[q] = (int64_t)m.giant_cycles[q];
   for (int q = 0; q < 5; ++q) stats.sparse_cycles[q] = (int64_t)m.sparse_cycles[q];
   stats.max_row_work = m.max_row_work;
   if (evs.on) {

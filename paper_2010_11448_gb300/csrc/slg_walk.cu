@@ -813,6 +813,7 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
     __syncthreads();
     const int32_t e = s_misc[0];
     if (e < 0) break;
+    const long long row_t0 = clock64();
     const int32_t smin = s_of(a.row_s, a.smin, e);
     const int32_t f_lo = a.full_rows ? 0 : e + 1;
     // far ends lie in [f_lo, f_hi): below R, or below the end of e's member
@@ -1113,6 +1114,8 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
           if (!unweighted) a.stage_w[b + i] = tw[i];
         }
     }
+    if (threadIdx.x == 0 && dense)
+      atomicAdd(&meta->giant_cycles[3], (unsigned long long)(clock64() - row_t0));
   }
 }
 
