@@ -720,6 +720,20 @@ constexpr size_t giant_smem() {
          (size_t)(2 * kGiantNT + 1 + kGiantNT / 32 + 1) * 4 + (size_t)(kGiantList + 1) * 4;
 }
 
+// Drops from L2, without writing them back to DRAM, the 128-byte lines that
+// lie wholly inside [p, p + n) (PTX discard.global.L2): for per-CTA scratch
+// whose contents are dead.  Every reader of the range must have passed a
+// block barrier since its last read; lines that the range shares with
+// neighbouring data at its two ends are left alone.
+__device__ __forceinline__ void l2_discard(const int32_t *p, long long n) {
+  if (n <= 0) return;
+  const unsigned long long g = (unsigned long long)__cvta_generic_to_global(p);
+  const unsigned long long b = (g + 127ull) & ~127ull;
+  const unsigned long long e = (g + 4ull * (unsigned long long)n) & ~127ull;
+  for (unsigned long long x = b + 128ull * threadIdx.x; x < e; x += 128ull * blockDim.x)
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(x) : "memory");
+}
+
 // Exclusive scan of the kNSB sub-range counters in place (P per thread);
 // returns the total.
 __device__ __forceinline__ int32_t scan_subranges(int32_t *a, int32_t *ws) {
@@ -928,6 +942,7 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
           if (f >= F0 && f < F1) wl[atomicAdd(sub + ((f - F0) >> shift), 1)] = f;
         });
         __syncthreads();
+        if (F1 == f_hi) l2_discard(flat, work);  // the flattened copy's last read
         // now sub[b] = end of the wedges of sub-range b; subt[b] = start of its
         // items.  3. bucket starts: sub-range b opens a bucket when its start
         // in the merged order (wedges + items before it) / cap changes.
@@ -1097,6 +1112,8 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
           };
           if (!hash_bucket(b0, b1, lo, hi, nit)) break;
         }
+        __syncthreads();
+        l2_discard(wl, nw);  // the super-chunk's grouped far ends are consumed
         clk_bucket += clock64() - c1;
       }
       if (threadIdx.x == 0) {
@@ -1113,6 +1130,9 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
           a.stage_j[b + i] = tj[i];
           if (!unweighted) a.stage_w[b + i] = tw[i];
         }
+      __syncthreads();
+      l2_discard(tj, out);  // the row's pairs are in the staging area
+      if (!unweighted) l2_discard(tw, out);
     }
     if (threadIdx.x == 0 && dense)
       atomicAdd(&meta->giant_cycles[3], (unsigned long long)(clock64() - row_t0));
