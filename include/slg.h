@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define SLG_ABI_VERSION 6
+#define SLG_ABI_VERSION 7
 
 /* Incidence of H as CSR + CSC (Section III: the hyperedge/vertex incidence
  * and its bipartite form).  All pointers are device pointers. */
@@ -105,6 +105,11 @@ typedef enum slg_status {
 #define SLG_ASYNC 0x40u      /* slg_build_host only: return once the copies
                                 of the result to the host are enqueued on
                                 `stream` (see slg_build_host) */
+#define SLG_W16 0x80u        /* slg_build_host_many queries only: out_w is a
+                                HOST uint16 array; the weights |e ∩ f| are
+                                narrowed on the device before the copy back
+                                (exact: a weight above 65,535 makes the
+                                query fail with SLG_ERR_UNSUPPORTED) */
 /* Algorithm selector (mutually exclusive values in bits 8..11). */
 #define SLG_ALGO_MASK 0xF00u
 #define SLG_ALGO_BINNED 0x000u /* default: degree-binned wedge walk */
@@ -206,7 +211,8 @@ int slg_build_csr(const slg_hypergraph *h, int32_t s, uint32_t flags,
 
 /*
  * One query of slg_build_host_many: L_s of the hypergraph or of its dual.
- *   s, flags   as for slg_build (SLG_ASYNC is not accepted)
+ *   s, flags   as for slg_build (SLG_ASYNC is not accepted), plus SLG_W16
+ *              (out_w then points to uint16 host memory)
  *   row_ptr    HOST int64 array of R + 1 entries for the compressed row form
  *              of slg_build_csr (out_i unused, may be NULL), or NULL for the
  *              (i, j, w) triples of slg_build

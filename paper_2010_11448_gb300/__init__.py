@@ -38,6 +38,7 @@ SLG_RELABEL_ASC = 0x8
 SLG_RELABEL_DESC = 0x10
 SLG_NO_PRUNE = 0x20
 SLG_ASYNC = 0x40
+SLG_W16 = 0x80
 SLG_ALGO_BINNED = 0x000
 SLG_ALGO_PLAIN = 0x100
 SLG_ALGO_SPGEMM = 0x200
@@ -401,14 +402,15 @@ def build_host_many(h, queries, stream=None):
     """Several builds of one host hypergraph (slg_build_host_many): the
     incidence is copied to the device once and each result is copied back
     while the next is built.  ``queries``: dicts with keys s, dual,
-    unweighted (optional), algo (optional), capacity, and host arrays
-    row_ptr (int64[R + 1]; compressed row form) or out_i, plus out_j, out_w.
-    Returns a list of (status, n_pairs)."""
+    unweighted (optional), algo (optional), w16 (optional: out_w is a
+    16-bit host array and receives the weights as uint16), capacity, and
+    host arrays row_ptr (int64[R + 1]; compressed row form) or out_i, plus
+    out_j, out_w.  Returns a list of (status, n_pairs)."""
     qs = (_Query * len(queries))()
     for k, q in enumerate(queries):
         qs[k].s = int(q["s"])
         qs[k].flags = _flags(q.get("dual", False), q.get("unweighted", False),
-                             q.get("algo", "binned"))
+                             q.get("algo", "binned")) | (SLG_W16 if q.get("w16") else 0)
         qs[k].row_ptr = _hptr(q.get("row_ptr"))
         qs[k].out_i = _hptr(q.get("out_i"))
         qs[k].out_j = _hptr(q.get("out_j"))

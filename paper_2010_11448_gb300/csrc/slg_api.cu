@@ -991,11 +991,14 @@ int upload(const slg_hypergraph *hh, Pool &pool, cudaStream_t st, slg_hypergraph
 // once the build is done (the device buffers are released on `cs` after
 // them).  Returns the query's status.
 int host_query(const slg_hypergraph *d, slg_query *q, cudaStream_t st, cudaStream_t cs,
-               cudaEvent_t done, std::vector<void *> *keep) {
+               cudaEvent_t done, std::vector<void *> *keep, int32_t *bad) {
   q->n_pairs = 0;
-  const uint32_t flags = q->flags;
-  if (flags & SLG_ASYNC) return SLG_ERR_INVALID;
-  const bool unweighted = (flags & SLG_UNWEIGHTED) != 0;
+  if (q->flags & SLG_ASYNC) return SLG_ERR_INVALID;
+  const bool unweighted = (q->flags & SLG_UNWEIGHTED) != 0;
+  // SLG_W16: the weights are narrowed on the device (into buf[4]) and
+  // copied back as uint16; *bad is set when one does not fit
+  const bool w16 = (q->flags & SLG_W16) != 0 && !unweighted;
+  const uint32_t flags = q->flags & ~(uint32_t)SLG_W16;
   const bool rows_form = q->row_ptr != nullptr;
   if (q->capacity < 0) return SLG_ERR_INVALID;
   if (q->capacity > 0 &&
@@ -1003,7 +1006,7 @@ int host_query(const slg_hypergraph *d, slg_query *q, cudaStream_t st, cudaStrea
     return SLG_ERR_INVALID;
   const int32_t R = (flags & SLG_DUAL) ? d->n_vertices : d->n_edges;
   cudaMemPool_t mem = lib_pool();
-  void *buf[4] = {nullptr, nullptr, nullptr, nullptr};
+  void *buf[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   auto alloc = [&](int k, size_t bytes) {
     bytes = bytes < 16 ? 16 : bytes;
     cudaError_t e = mem ? cudaMallocFromPoolAsync(&buf[k], bytes, mem, st)
@@ -1026,6 +1029,7 @@ int host_query(const slg_hypergraph *d, slg_query *q, cudaStream_t st, cudaStrea
     if (e == cudaSuccess && !unweighted) e = alloc(2, cap * 4);
   }
   if (e == cudaSuccess && rows_form) e = alloc(3, ((size_t)R + 1) * 8);
+  if (e == cudaSuccess && w16 && cap > 0) e = alloc(4, cap * 2);
   if (e != cudaSuccess) {
     release(st);
     return status_of(e);
@@ -1038,6 +1042,13 @@ int host_query(const slg_hypergraph *d, slg_query *q, cudaStream_t st, cudaStrea
   if (rc != SLG_OK) {
     release(st);
     return rc;
+  }
+  if (w16 && pairs > 0 &&
+      launch_pack_w16(static_cast<const int32_t *>(buf[2]), pairs,
+                      static_cast<uint16_t *>(buf[4]), bad, st) != cudaSuccess) {
+    cudaGetLastError();
+    release(st);
+    return SLG_ERR_CUDA;
   }
   // the copies back wait for the build (the stream already synchronised
   // inside run; the event keeps the order explicit for the copy stream)
@@ -1055,7 +1066,8 @@ int host_query(const slg_hypergraph *d, slg_query *q, cudaStream_t st, cudaStrea
       c = cudaMemcpyAsync(q->out_i, buf[0], p * 4, cudaMemcpyDeviceToHost, cs);
     if (c == cudaSuccess) c = cudaMemcpyAsync(q->out_j, buf[1], p * 4, cudaMemcpyDeviceToHost, cs);
     if (c == cudaSuccess && !unweighted)
-      c = cudaMemcpyAsync(q->out_w, buf[2], p * 4, cudaMemcpyDeviceToHost, cs);
+      c = w16 ? cudaMemcpyAsync(q->out_w, buf[4], p * 2, cudaMemcpyDeviceToHost, cs)
+              : cudaMemcpyAsync(q->out_w, buf[2], p * 4, cudaMemcpyDeviceToHost, cs);
   }
   // the buffers stay until every copy of the call is done and are then
   // released on `st`, so that the pool hands them to the next call on `st`
@@ -1199,24 +1211,40 @@ int slg_build_host_many(const slg_hypergraph *hh, slg_query *queries, int32_t co
     cudaStreamDestroy(cs);
     return SLG_ERR_CUDA;
   }
+  // one flag per query: a weight too large for SLG_W16
+  int32_t *bad = nullptr;
+  cudaError_t eb = pool.get(&bad, (size_t)count);
+  if (eb == cudaSuccess) eb = cudaMemsetAsync(bad, 0, sizeof(int32_t) * (size_t)count, st);
+  if (eb != cudaSuccess) {
+    cudaGetLastError();
+    cudaEventDestroy(done);
+    cudaStreamDestroy(cs);
+    return status_of(eb);
+  }
   int first = SLG_OK;
   std::vector<void *> keep;
   for (int32_t k = 0; k < count; ++k) {
-    const int q = host_query(&d, &queries[k], st, cs, done, &keep);
+    const int q = host_query(&d, &queries[k], st, cs, done, &keep, bad + k);
     queries[k].status = q;
-    if (q != SLG_OK && first == SLG_OK) first = q;
   }
   // every copy back done, then the device outputs and the uploaded input
   // (Pool) are released on `st`
   cudaError_t e1 = cudaEventRecord(done, cs);
   if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(st, done, 0);
   for (void *b : keep) cudaFreeAsync(b, st);
+  std::vector<int32_t> bad_h((size_t)count, 0);
+  const cudaError_t e3 = cudaMemcpyAsync(bad_h.data(), bad, sizeof(int32_t) * (size_t)count,
+                                         cudaMemcpyDeviceToHost, st);
   const cudaError_t e2 = cudaStreamSynchronize(st);
   cudaEventDestroy(done);
   cudaStreamDestroy(cs);
-  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
     cudaGetLastError();
     return SLG_ERR_CUDA;
+  }
+  for (int32_t k = 0; k < count; ++k) {
+    if (queries[k].status == SLG_OK && bad_h[k]) queries[k].status = SLG_ERR_UNSUPPORTED;
+    if (queries[k].status != SLG_OK && first == SLG_OK) first = queries[k].status;
   }
   return first;
 }

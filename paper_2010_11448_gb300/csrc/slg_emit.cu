@@ -112,11 +112,47 @@ __global__ __launch_bounds__(kNT) void k_gather(int32_t row_begin, int32_t rows,
   }
 }
 
+// w16[i] = w[i] for i < n, 8 weights per thread step (two 16-byte loads, one
+// 16-byte store); a weight above 65,535 sets *bad.  Both arrays start on a
+// 16-byte boundary (pool allocations).
+__global__ __launch_bounds__(kNT) void k_pack_w16(const int32_t *__restrict__ w, long long n,
+                                                  uint16_t *__restrict__ w16,
+                                                  int32_t *__restrict__ bad) {
+  const long long n8 = n >> 3;
+  const long long stride = (long long)gridDim.x * kNT;
+  bool over = false;
+  for (long long q = (long long)blockIdx.x * kNT + threadIdx.x; q < n8; q += stride) {
+    const int4 a = reinterpret_cast<const int4 *>(w)[2 * q];
+    const int4 b = reinterpret_cast<const int4 *>(w)[2 * q + 1];
+    over |= ((uint32_t)(a.x | a.y | a.z | a.w | b.x | b.y | b.z | b.w) > 0xFFFFu);
+    uint4 o;
+    o.x = (uint32_t)(a.x & 0xFFFF) | ((uint32_t)a.y << 16);
+    o.y = (uint32_t)(a.z & 0xFFFF) | ((uint32_t)a.w << 16);
+    o.z = (uint32_t)(b.x & 0xFFFF) | ((uint32_t)b.y << 16);
+    o.w = (uint32_t)(b.z & 0xFFFF) | ((uint32_t)b.w << 16);
+    reinterpret_cast<uint4 *>(w16)[q] = o;
+  }
+  for (long long i = (n8 << 3) + (long long)blockIdx.x * kNT + threadIdx.x; i < n; i += stride) {
+    over |= ((uint32_t)w[i] > 0xFFFFu);
+    w16[i] = (uint16_t)w[i];
+  }
+  if (over) *bad = 1;
+}
+
 __global__ void k_meta_copy(const uint32_t *__restrict__ src, volatile uint32_t *dst, int n) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
 }  // namespace
+
+cudaError_t launch_pack_w16(const int32_t *w, int64_t n, uint16_t *w16, int32_t *bad,
+                            cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const long long groups = (n + 7) / 8;
+  const int blocks = (int)std::min<long long>((groups + kNT - 1) / kNT, 152 * 8);
+  k_pack_w16<<<blocks, kNT, 0, st>>>(w, n, w16, bad);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_meta_copy(const Meta *src, Meta *dst, cudaStream_t st) {
   static_assert(sizeof(Meta) % 4 == 0, "Meta is copied as 32-bit words");

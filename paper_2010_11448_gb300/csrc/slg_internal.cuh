@@ -478,6 +478,9 @@ cudaError_t launch_row_scan(int32_t rows, const Work &w, cudaStream_t st);
 // The device Meta into host memory the device can address (mapped pinned
 // memory), by a kernel: no copy engine involved.
 cudaError_t launch_meta_copy(const Meta *src, Meta *dst, cudaStream_t st);
+// w16[i] = w[i] (i < n); *bad = 1 if a weight is above 65,535.
+cudaError_t launch_pack_w16(const int32_t *w, int64_t n, uint16_t *w16, int32_t *bad,
+                            cudaStream_t st);
 // out_cap: entries of the output arrays (a row beyond them raises an error).
 cudaError_t launch_gather(int32_t row_begin, int32_t rows, const Work &w, int32_t *out_i,
                           int32_t *out_j, int32_t *out_w, int unweighted, long long out_cap,

@@ -439,3 +439,66 @@ def test_build_host_csr_entry_point(medium):
         assert slg.load().slg_build_host_csr(ctypes.byref(st), 4, flags, ptr.ctypes.data,
                                              j.ctypes.data, w.ctypes.data, j.shape[0],
                                              ctypes.byref(n), None) == 6
+
+
+def _host_h(h):
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.int32)).pin_memory()
+
+    class HostH:
+        pass
+    hh = HostH()
+    hh.m, hh.n = h.m, h.n
+    hh.e_off, hh.e_idx, hh.v_off, hh.v_idx = (pin(h.e_off), pin(h.e_idx), pin(h.v_off),
+                                              pin(h.v_idx))
+    return hh
+
+
+def test_build_host_many_w16(medium):
+    # SLG_W16: the same lists with the weights returned as uint16
+    h, _ = medium
+    hh = _host_h(h)
+    jobs = [(True, 2, True), (False, 3, False)]
+    wants = [want_lg(h, s, dual) for dual, s, _ in jobs]
+    queries = []
+    for (dual, s, csr), want in zip(jobs, wants):
+        cap = want.shape[0] + 2
+        q = {"s": s, "dual": dual, "capacity": cap, "w16": True,
+             "out_j": torch.full((cap,), -1, dtype=torch.int32).pin_memory(),
+             "out_w": torch.full((cap,), -1, dtype=torch.int16).pin_memory()}
+        if csr:
+            q["row_ptr"] = torch.zeros((h.n if dual else h.m) + 1, dtype=torch.int64).pin_memory()
+        else:
+            q["out_i"] = torch.zeros(cap, dtype=torch.int32).pin_memory()
+        queries.append(q)
+    res = slg.build_host_many(hh, queries)
+    assert [r[0] for r in res] == [0, 0]
+    for (dual, s, csr), want, q, (_, n) in zip(jobs, wants, queries, res):
+        assert n == want.shape[0]
+        w = q["out_w"][:n].numpy().view(np.uint16).astype(np.int64)
+        if csr:
+            got = _csr_to_triples(q["row_ptr"].numpy(), q["out_j"][:n].numpy(), w)
+        else:
+            got = np.stack([q["out_i"][:n].numpy(), q["out_j"][:n].numpy(), w], 1).astype(np.int64)
+        assert np.array_equal(got, want), (dual, s)
+        assert int(q["out_w"][n]) == -1  # nothing past the pairs
+
+
+def test_build_host_many_w16_overflow():
+    # two hyperedges sharing 70,000 vertices: w = 70,000 does not fit 16 bits,
+    # so that query fails with SLG_ERR_UNSUPPORTED; a 32-bit query of the same
+    # call and a later 16-bit one (s above every weight: no pairs) are
+    # unaffected
+    n = 70_010
+    shared = list(range(70_000))
+    h = hg.from_rows([shared + [70_000], shared + [70_001], [70_002, 70_003], [70_002, 70_003]], n)
+    hh = _host_h(h)
+
+    def q(w16, s):
+        return {"s": s, "dual": False, "capacity": 4, "w16": w16,
+                "out_i": np.zeros(4, np.int32), "out_j": np.zeros(4, np.int32),
+                "out_w": np.zeros(4, np.int16 if w16 else np.int32)}
+    qs = [q(True, 2), q(False, 2), q(True, 70_001)]
+    res = slg.build_host_many(hh, qs)
+    assert res[0] == (6, 2) and res[1] == (0, 2) and res[2] == (0, 0)
+    assert qs[1]["out_i"][:2].tolist() == [0, 2] and qs[1]["out_j"][:2].tolist() == [1, 3]
+    assert qs[1]["out_w"][:2].tolist() == [70_000, 2]
