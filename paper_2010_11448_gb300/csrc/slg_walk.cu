@@ -636,13 +636,10 @@ __device__ __forceinline__ void sp_candidate(unsigned long long *tab, uint32_t *
   *(volatile int32_t *)s_ovf = 1;
 }
 
-// Pass 2: one wedge to f; counted when f is a candidate.  Unweighted: a
-// count that reached s is not raised further.
-__device__ __forceinline__ void sp_count(unsigned long long *tab, const uint32_t *cand,
-                                         int32_t f, int32_t smin, bool unweighted, int lgb,
-                                         int lgt) {
-  const uint32_t c = sp_h2(f, lgb);
-  if (!(cand[c >> 5] & (1u << (c & 31)))) return;
+// Pass 2, for an f that passed the candidate filter: counted if it is in
+// the table.  Unweighted: a count that reached s is not raised further.
+__device__ __forceinline__ void sp_count_listed(unsigned long long *tab, int32_t f, int32_t smin,
+                                                bool unweighted, int lgt) {
   const uint32_t mask = (1u << lgt) - 1u;
   uint32_t h = sp_ht(f, lgt);
   for (int probe = 0; probe < kSpMaxProbe; ++probe) {
@@ -655,6 +652,31 @@ __device__ __forceinline__ void sp_count(unsigned long long *tab, const uint32_t
     if (k == 0xFFFFFFFFu) return;
     h = (h + 1) & mask;
   }
+}
+
+// Pass 2: one wedge to f; counted when f is a candidate.
+__device__ __forceinline__ void sp_count(unsigned long long *tab, const uint32_t *cand,
+                                         int32_t f, int32_t smin, bool unweighted, int lgb,
+                                         int lgt) {
+  const uint32_t c = sp_h2(f, lgb);
+  if (!(cand[c >> 5] & (1u << (c & 31)))) return;
+  sp_count_listed(tab, f, smin, unweighted, lgt);
+}
+
+// A lane's few wedges of a walk step that take the slow path (candidate
+// claims in pass 1, counts in pass 2: a small fraction of the wedges) are
+// gathered in registers and handled in rounds, the q-th round taking every
+// lane's q-th one, so that a warp runs max over its lanes rounds instead of
+// one round per wedge slot of the step with a lane or two active.
+#ifndef SLG_SP_DEFER
+#define SLG_SP_DEFER 1
+#endif
+template <int G>
+__device__ __forceinline__ void pend_push(int32_t (&pend)[G], int &np, bool c, int32_t f, int g) {
+#pragma unroll
+  for (int q = 0; q < G; ++q)  // selects: no local memory
+    if (q <= g) pend[q] = (c && q == np) ? f : pend[q];
+  np += c;
 }
 
 // ------------------------------------------------------------- giant bin --
@@ -1207,9 +1229,21 @@ __global__ __launch_bounds__(kSpNT, SLG_SP_MINB) void k_walk_sparse(
             m[g] = f[g] >= 0 ? 1u << (h & 31) : 0u;
             old[g] = f[g] >= 0 ? atomicOr(filt + (h >> 5), m[g]) : 0u;
           }
+#if SLG_SP_DEFER
+          int32_t pend[kSpG] = {};
+          int np = 0;
+#pragma unroll
+          for (int g = 0; g < kSpG; ++g) pend_push(pend, np, (old[g] & m[g]) != 0, f[g], g);
+#pragma unroll
+          for (int q = 0; q < kSpG; ++q) {
+            if (!__any_sync(0xffffffffu, q < np)) break;
+            if (q < np) sp_candidate(tab, cand, pend[q], s_ovf, lgb, lgt);
+          }
+#else
 #pragma unroll
           for (int g = 0; g < kSpG; ++g)
             if (old[g] & m[g]) sp_candidate(tab, cand, f[g], s_ovf, lgb, lgt);
+#endif
         });
     __syncthreads();  // candidates final
     {
@@ -1235,9 +1269,28 @@ __global__ __launch_bounds__(kSpNT, SLG_SP_MINB) void k_walk_sparse(
     } else {
       cta_walk_batched<kSpNT, kSpG>(
           w, k0, k1, s_beg, s_pref, ws, [&](const int32_t(&f)[kSpG], int32_t) {
+#if SLG_SP_DEFER
+            uint32_t word[kSpG], bit[kSpG];
+#pragma unroll
+            for (int g = 0; g < kSpG; ++g) {  // the candidate filter, loads in flight together
+              const uint32_t c = sp_h2(f[g], lgb);
+              bit[g] = 1u << (c & 31);
+              word[g] = f[g] >= 0 ? cand[c >> 5] : 0u;
+            }
+            int32_t pend[kSpG] = {};
+            int np = 0;
+#pragma unroll
+            for (int g = 0; g < kSpG; ++g) pend_push(pend, np, (word[g] & bit[g]) != 0, f[g], g);
+#pragma unroll
+            for (int q = 0; q < kSpG; ++q) {
+              if (!__any_sync(0xffffffffu, q < np)) break;
+              if (q < np) sp_count_listed(tab, pend[q], smin, unweighted, lgt);
+            }
+#else
 #pragma unroll
             for (int g = 0; g < kSpG; ++g)
               if (f[g] >= 0) sp_count(tab, cand, f[g], smin, unweighted, lgb, lgt);
+#endif
           });
     }
     __syncthreads();  // counts final
