@@ -722,6 +722,12 @@ constexpr int kNSB = 1 << kNSBLog;  // sub-ranges per super-chunk
 constexpr int kShiftMax = 31 - __builtin_clz(kGiantTMax / 4);  // 2^shift <= kGiantTMax / 4
 constexpr int kGiantSPT = kGiantTMax / kGiantNT;
 constexpr int kDenseW = 2 * kGiantTMax;  // ids per dense window (int32 counters in the table)
+// ids per dense window with 16-bit counters (rows of at most 65,535 vertices:
+// a count |e ∩ f| never exceeds |e|)
+constexpr int kDenseW16 = 4 * kGiantTMax;
+#ifndef SLG_DENSE16
+#define SLG_DENSE16 1
+#endif
 
 constexpr int kGiantList = kGiantTMax / 2;  // survivors of a bucket (<= its distinct keys)
 #ifndef SLG_GIANT_DIRECT_MAX
@@ -863,6 +869,9 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
     // Dense rows (at least one wedge per 8 ids) count fixed windows of
     // kDenseW ids in a dense shared array: no hashing, no sort.
     const bool dense = (long long)work * a.dense_ratio >= (long long)span;
+    // dense rows with 16-bit counters: twice the ids per window
+    const bool d16 = SLG_DENSE16 && dense && w.r_off[e + 1] - w.r_off[e] <= 0xFFFF;
+    const int32_t dwin = d16 ? kDenseW16 : kDenseW;
     if (work > q4) {  // the scratch is sized by the largest row: cannot happen
       if (threadIdx.x == 0) raise_error(meta, SLG_ERR_INVALID, kWhereGiant);
       break;
@@ -977,7 +986,7 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
             flag[q] = 0;
             if (b < nsb) {
               if (dense) {
-                flag[q] = ((b << shift) & (kDenseW - 1)) == 0;
+                flag[q] = ((b << shift) & (dwin - 1)) == 0;
               } else {
                 const int32_t st = (b ? sub[b - 1] : 0) + (core_row ? subt[b] : 0);
                 const int32_t sp = b ? (b > 1 ? sub[b - 2] : 0) + (core_row ? subt[b - 1] : 0) : 0;
@@ -1017,6 +1026,97 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
             __syncthreads();
           }
           if (hi - lo + nit == 0) continue;  // uniform
+          if (d16) {
+            // 16-bit counters, two per word; the emission scans 8 counters
+            // per 16-byte load and reads a counter again only for survivors
+            const int32_t fb0 = F0 + (b0 << shift);
+            const int32_t dw = min((b1 - b0) << shift, F1 - fb0);  // <= kDenseW16
+            uint32_t *c32 = reinterpret_cast<uint32_t *>(tab);
+            const uint16_t *c16 = reinterpret_cast<const uint16_t *>(tab);
+            uint4 *c128 = reinterpret_cast<uint4 *>(tab);
+            for (int32_t i = threadIdx.x; i < (dw + 7) / 8; i += kGiantNT)
+              c128[i] = make_uint4(0, 0, 0, 0);
+            __syncthreads();
+            for_each_batched<kGiantNT, 8>(wl, lo, hi, [&](int32_t f) {
+              const int32_t o = f - fb0;
+              atomicAdd(c32 + (o >> 1), 1u << ((o & 1) << 4));
+            });
+            if (core_row && nit > 0)
+              for (int32_t p = s_misc[2] + (int32_t)threadIdx.x; p < s_misc[3]; p += kGiantNT) {
+                const int32_t f = ci.core_list[p];
+                const int32_t wt = Trow[p];
+                if (wt > 0 && w.r_off[f + 1] - w.r_off[f] >= smin) {
+                  const int32_t o = f - fb0;
+                  atomicAdd(c32 + (o >> 1), (uint32_t)wt << ((o & 1) << 4));
+                }
+              }
+            __syncthreads();
+            // warp q owns counters [q * span_w, (q + 1) * span_w); lane l
+            // takes the groups of 8 at q0 + 8 (l + 32 k), k < span_w / 256
+            const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+            constexpr int NWq = kGiantNT / 32;
+            constexpr int KMAX = kDenseW16 / NWq / 256;  // groups per lane at most
+            const int32_t span_w = ((dw + NWq - 1) / NWq + 255) & ~255;
+            const int32_t q0 = wq * span_w, q1 = min(dw, q0 + span_w);
+            const int32_t nk = span_w >> 8;
+            const uint32_t s2 = (uint32_t)min(smin, 0xFFFF) * 0x10001u;
+            uint32_t mk[KMAX];
+            int32_t c = 0;
+  #pragma unroll
+            for (int k = 0; k < KMAX; ++k) {
+              mk[k] = 0;
+              const int32_t i8 = q0 + ((lane + (k << 5)) << 3);
+              if (k < nk && i8 < q1) {
+                const uint4 v = c128[i8 >> 3];
+                // per 16-bit counter: 0xFFFF where count >= smin
+                const uint32_t g0 = __vcmpgeu2(v.x, s2), g1 = __vcmpgeu2(v.y, s2);
+                const uint32_t g2 = __vcmpgeu2(v.z, s2), g3 = __vcmpgeu2(v.w, s2);
+                mk[k] = (g0 & 1u) | ((g0 >> 15) & 2u) | ((g1 & 1u) << 2) | ((g1 >> 13) & 8u) |
+                        ((g2 & 1u) << 4) | ((g2 >> 11) & 32u) | ((g3 & 1u) << 6) |
+                        ((g3 >> 9) & 128u);
+                c += __popc(mk[k]);
+              }
+            }
+  #pragma unroll
+            for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+            int32_t total;
+            const int32_t winc = block_inclusive_scan<kGiantNT>(lane == 0 ? c : 0, ws, &total);
+            int32_t pos = out + __shfl_sync(0xffffffffu, winc, 0) - c;  // warp's first slot
+            if (a.mode == kStage && out + total > q4) {
+              if (threadIdx.x == 0) raise_error(meta, SLG_ERR_INVALID, kWhereGiant);
+              break;
+            }
+            if (emit && total > 0) {
+  #pragma unroll
+              for (int k = 0; k < KMAX; ++k) {
+                if (k >= nk) break;  // warp-uniform
+                uint32_t m = mk[k];
+                const int32_t cnt = __popc(m);
+                const int32_t inc = warp_inclusive_scan(cnt);
+                int32_t t = pos + inc - cnt;
+                pos += __shfl_sync(0xffffffffu, inc, 31);
+                const int32_t i8 = q0 + ((lane + (k << 5)) << 3);
+                while (m) {
+                  const int b = __ffs(m) - 1;
+                  m &= m - 1;
+                  const int32_t i = i8 + b;
+                  const int32_t n = c16[i];
+                  if (a.mode == kDirect) {
+                    put(a, base, t, e, fb0 + i, n);
+                  } else {
+                    tj[t] = fb0 + i;
+                    if (!unweighted) tw[t] = n;
+                  }
+                  ++t;
+                }
+              }
+            }
+            out += total;
+            __syncthreads();
+            for (int32_t i = threadIdx.x; i < (dw + 3) / 4; i += kGiantNT) tab[i] = kEmpty64;
+            __syncthreads();
+            continue;
+          }
           if (dense) {
             const int32_t fb0 = F0 + (b0 << shift);
             const int32_t dw = min((b1 - b0) << shift, F1 - fb0);  // <= kDenseW
