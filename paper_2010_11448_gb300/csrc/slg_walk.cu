@@ -740,6 +740,18 @@ constexpr int kGiantG = 6;  // wedges per thread per step of the giant bin's wal
 static_assert(kGiantDirectMax <= kGiantTMax && kGiantDirectMax / 2 <= kGiantList,
               "a direct row fits the table and the survivor list");
 constexpr int kGiantQ = kGiantList / kGiantNT;
+// Survivor sets of up to this many keys are ordered in the survivor-list
+// area (kGiantList ints = kGiantList / 2 keys): the keys start past the
+// slot indices (ceil(n / 2) keys) and the run sort needs 32 ceil(n / 32) + n
+// more.
+#ifndef SLG_GIANT_LIST_SORT
+#define SLG_GIANT_LIST_SORT 1
+#endif
+constexpr int32_t kGiantListSortMax = 800;
+static_assert((kGiantListSortMax + 1) / 2 + 32 * ((kGiantListSortMax + 31) / 32) +
+                      kGiantListSortMax <= kGiantList / 2,
+              "the list area holds the ordering of kGiantListSortMax keys");
+static_assert(kGiantListSortMax <= 8 * kGiantNT, "the run sort covers the list sort");
 
 // [s_base 16][s_misc 16][table TMAX x 8][sub NSB][subt NSB+1][bstart NSB+1]
 // [s_beg NT][s_pref NT+1][ws NT/32+1][list kGiantList][list count 1]
@@ -747,6 +759,10 @@ constexpr size_t giant_smem() {
   return 32 + (size_t)kGiantTMax * 8 + (size_t)(3 * kNSB + 2) * 4 +
          (size_t)(2 * kGiantNT + 1 + kGiantNT / 32 + 1) * 4 + (size_t)(kGiantList + 1) * 4;
 }
+// The survivor list starts on an 8-byte boundary (it also holds 64-bit keys).
+static_assert((32 + (size_t)kGiantTMax * 8 + (size_t)(3 * kNSB + 2) * 4 +
+               (size_t)(2 * kGiantNT + 1 + kGiantNT / 32 + 1) * 4) % 8 == 0,
+              "survivor list alignment");
 
 // Drops from L2, without writing them back to DRAM, the 128-byte lines that
 // lie wholly inside [p, p + n) (PTX discard.global.L2): for per-CTA scratch
@@ -1198,6 +1214,29 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
             table_reset_front<kGiantNT>(tab, used);
             return true;
           };
+          // the sorted pairs keys[0, total) of a bucket, ordered outside the
+          // table (which is already clear), go to the row's output; false
+          // (uniform) when they would not fit the scratch
+          auto emit_keys = [&](const unsigned long long *keys, int32_t total) -> bool {
+            if (a.mode == kStage && out + total > q4) {
+              if (threadIdx.x == 0) raise_error(meta, SLG_ERR_INVALID, kWhereGiant);
+              __syncthreads();
+              return false;
+            }
+            for (int32_t i = threadIdx.x; i < total; i += kGiantNT) {
+              const unsigned long long x = keys[i];
+              const int32_t f = (int32_t)(x >> 32), n = (int32_t)(uint32_t)x;
+              if (a.mode == kDirect) {
+                put(a, base, out + i, e, f, n);
+              } else {
+                tj[out + i] = f;
+                if (!unweighted) tw[out + i] = n;
+              }
+            }
+            out += total;
+            __syncthreads();  // the keys are read before the next bucket fills the list
+            return true;
+          };
           // sub-ranges [h0, h1) (wedges wl[hlo, hhi), tile items `hnit`)
           // counted in the hash table
           auto hash_bucket = [&](int32_t h0, int32_t h1, int32_t hlo, int32_t hhi,
@@ -1224,6 +1263,25 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
             int32_t at = 0, used = T, total;
             if (list) {
               insert_all(std::true_type{});
+#if SLG_GIANT_LIST_SORT
+              // Survivors ordered in the survivor-list area, past their slot
+              // indices, while the table is cleared: no front region of the
+              // table to clear afterwards, two block barriers fewer per bucket.
+              __syncthreads();  // inserts done: the list is final
+              const int32_t nl = min(*sl.n, sl.cap);
+              if (emit && nl <= kGiantListSortMax) {  // uniform
+                unsigned long long *lk =
+                    reinterpret_cast<unsigned long long *>(sl.slot) + ((nl + 1) >> 1);
+                for (int32_t i = threadIdx.x; i < nl; i += kGiantNT)
+                  lk[i] = tab[sl.slot[i]] + 1ull;  // the count word holds count - 1
+                __syncthreads();  // keys in place; every table and slot read done
+                clear_slots<kGiantNT>(tab, T);
+                if (threadIdx.x == 0) *sl.n = 0;
+                int32_t su;
+                const int32_t off = sort_survivors<kGiantNT>(lk, nl, &su);
+                return emit_keys(lk + off, nl);
+              }
+#endif
               total = table_collect_list<kGiantNT, kGiantQ>(tab, T, sl, emit, &at, &used);
             } else {
               insert_all(std::false_type{});
