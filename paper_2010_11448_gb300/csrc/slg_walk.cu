@@ -360,6 +360,38 @@ __device__ __forceinline__ int32_t sort_survivors(unsigned long long *tab, int32
   return 0;
 }
 
+// fn(r, x) for every key x of k[0, n) with r = the number of keys below x
+// (distinct keys): for n <= 64 by one broadcast pass, else from runs of 32
+// sorted in place (k[0, 32 ceil(n / 32)) is overwritten, padded with ~0)
+// and binary searches over them.  No barrier after the calls.
+template <int NT, class Fn>
+__device__ __forceinline__ void rank_keys(unsigned long long *k, int32_t n, Fn &&fn) {
+  if (n <= 64) {
+    for (int32_t i = threadIdx.x; i < n; i += NT) {
+      const unsigned long long x = k[i];
+      int32_t r = 0;
+      for (int32_t j = 0; j < n; ++j) r += k[j] < x;
+      fn(r, x);
+    }
+    return;
+  }
+  const int32_t nr = (n + 31) >> 5;
+  for (int32_t q = (int32_t)threadIdx.x >> 5; q < nr; q += NT / 32) {
+    const int32_t i = (q << 5) + (int32_t)(threadIdx.x & 31);
+    const unsigned long long x = warp_sort32(i < n ? k[i] : ~0ull);
+    k[i] = x;  // the run's loads precede the shuffles
+  }
+  __syncthreads();
+  // runs 0 .. nr-2 are full and the last one holds its keys first, so
+  // k[0, n) holds every key once
+  for (int32_t i = threadIdx.x; i < n; i += NT) {
+    const unsigned long long x = k[i];
+    int32_t r = 0;
+    for (int32_t q = 0; q < nr; ++q) r += run_below(k + (q << 5), x);
+    fn(r, x);
+  }
+}
+
 // Survivors by a pass over the table (used for s = 1, where every key
 // survives).
 // Rounds of RND slots per thread (slot = (round * RND + i) * NT + thread):
@@ -742,15 +774,14 @@ static_assert(kGiantDirectMax <= kGiantTMax && kGiantDirectMax / 2 <= kGiantList
 constexpr int kGiantQ = kGiantList / kGiantNT;
 // Survivor sets of up to this many keys are ordered in the survivor-list
 // area (kGiantList ints = kGiantList / 2 keys): the keys start past the
-// slot indices (ceil(n / 2) keys) and the run sort needs 32 ceil(n / 32) + n
-// more.
+// slot indices (ceil(n / 2) keys) and their runs take 32 ceil(n / 32).
 #ifndef SLG_GIANT_LIST_SORT
 #define SLG_GIANT_LIST_SORT 1
 #endif
-constexpr int32_t kGiantListSortMax = 800;
-static_assert((kGiantListSortMax + 1) / 2 + 32 * ((kGiantListSortMax + 31) / 32) +
-                      kGiantListSortMax <= kGiantList / 2,
-              "the list area holds the ordering of kGiantListSortMax keys");
+constexpr int32_t kGiantListSortMax = 1024;
+static_assert((kGiantListSortMax + 1) / 2 + 32 * ((kGiantListSortMax + 31) / 32) <=
+                  kGiantList / 2,
+              "the list area holds the runs of kGiantListSortMax keys");
 static_assert(kGiantListSortMax <= 8 * kGiantNT, "the run sort covers the list sort");
 
 // [s_base 16][s_misc 16][table TMAX x 8][sub NSB][subt NSB+1][bstart NSB+1]
@@ -1214,29 +1245,6 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
             table_reset_front<kGiantNT>(tab, used);
             return true;
           };
-          // the sorted pairs keys[0, total) of a bucket, ordered outside the
-          // table (which is already clear), go to the row's output; false
-          // (uniform) when they would not fit the scratch
-          auto emit_keys = [&](const unsigned long long *keys, int32_t total) -> bool {
-            if (a.mode == kStage && out + total > q4) {
-              if (threadIdx.x == 0) raise_error(meta, SLG_ERR_INVALID, kWhereGiant);
-              __syncthreads();
-              return false;
-            }
-            for (int32_t i = threadIdx.x; i < total; i += kGiantNT) {
-              const unsigned long long x = keys[i];
-              const int32_t f = (int32_t)(x >> 32), n = (int32_t)(uint32_t)x;
-              if (a.mode == kDirect) {
-                put(a, base, out + i, e, f, n);
-              } else {
-                tj[out + i] = f;
-                if (!unweighted) tw[out + i] = n;
-              }
-            }
-            out += total;
-            __syncthreads();  // the keys are read before the next bucket fills the list
-            return true;
-          };
           // sub-ranges [h0, h1) (wedges wl[hlo, hhi), tile items `hnit`)
           // counted in the hash table
           auto hash_bucket = [&](int32_t h0, int32_t h1, int32_t hlo, int32_t hhi,
@@ -1277,9 +1285,24 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
                 __syncthreads();  // keys in place; every table and slot read done
                 clear_slots<kGiantNT>(tab, T);
                 if (threadIdx.x == 0) *sl.n = 0;
-                int32_t su;
-                const int32_t off = sort_survivors<kGiantNT>(lk, nl, &su);
-                return emit_keys(lk + off, nl);
+                if (a.mode == kStage && out + nl > q4) {  // uniform
+                  if (threadIdx.x == 0) raise_error(meta, SLG_ERR_INVALID, kWhereGiant);
+                  __syncthreads();
+                  return false;
+                }
+                // each key goes straight to its ranked place in the row's output
+                rank_keys<kGiantNT>(lk, nl, [&](int32_t r, unsigned long long x) {
+                  const int32_t f = (int32_t)(x >> 32), n = (int32_t)(uint32_t)x;
+                  if (a.mode == kDirect) {
+                    put(a, base, out + r, e, f, n);
+                  } else {
+                    tj[out + r] = f;
+                    if (!unweighted) tw[out + r] = n;
+                  }
+                });
+                out += nl;
+                __syncthreads();  // the keys are read before the next bucket fills the list
+                return true;
               }
 #endif
               total = table_collect_list<kGiantNT, kGiantQ>(tab, T, sl, emit, &at, &used);
