@@ -361,12 +361,13 @@ __device__ __forceinline__ int32_t sort_survivors(unsigned long long *tab, int32
 }
 
 // fn(r, x) for every key x of k[0, n) with r = the number of keys below x
-// (distinct keys): for n <= 64 by one broadcast pass, else from runs of 32
+// (distinct keys): for n <= 64 (or always, without RUNS) by one broadcast
+// pass, else from runs of 32
 // sorted in place (k[0, 32 ceil(n / 32)) is overwritten, padded with ~0)
 // and binary searches over them.  No barrier after the calls.
-template <int NT, class Fn>
+template <int NT, bool RUNS = true, class Fn>
 __device__ __forceinline__ void rank_keys(unsigned long long *k, int32_t n, Fn &&fn) {
-  if (n <= 64) {
+  if (!RUNS || n <= 64) {
     for (int32_t i = threadIdx.x; i < n; i += NT) {
       const unsigned long long x = k[i];
       int32_t r = 0;
@@ -375,6 +376,7 @@ __device__ __forceinline__ void rank_keys(unsigned long long *k, int32_t n, Fn &
     }
     return;
   }
+  if constexpr (!RUNS) return;
   const int32_t nr = (n + 31) >> 5;
   for (int32_t q = (int32_t)threadIdx.x >> 5; q < nr; q += NT / 32) {
     const int32_t i = (q << 5) + (int32_t)(threadIdx.x & 31);
@@ -491,11 +493,18 @@ __device__ __forceinline__ void table_reset_front(unsigned long long *tab, int32
 
 // -------------------------------------------------------------- CTA bins --
 
+#ifndef SLG_CTA_LIST_SORT
+#define SLG_CTA_LIST_SORT 1
+#endif
 template <int NT, int TMAX>
 struct CtaCfg {
   static constexpr int kSPT = TMAX / NT;  // slots per thread at most
   static constexpr int kList = TMAX / 4;  // survivors of a row when s >= 2 (<= work / 2)
   static constexpr int kQ = (kList + NT - 1) / NT;
+  // survivor sets ranked in the list area: ceil(n / 2) + n keys <= kList / 2
+  static constexpr int kListSortMax = kList / 3;
+  static_assert((16 + TMAX * 8 + (2 * NT + 1 + NT / 32 + 1) * 4) % 8 == 0,
+                "the survivor list starts on an 8-byte boundary");
   // [s_base 16 B][table TMAX x 8 B][s_beg NT][s_pref NT+1][ws NT/32+1]
   // [list kList][list count 1]
   static constexpr size_t smem() {
@@ -538,6 +547,27 @@ __global__ __launch_bounds__(NT, MINB) void k_walk_cta(Walk w, const int32_t *__
       cta_walk<NT, 4>(w, k0, k1, s_beg, s_pref, ws, [&](int32_t f, int32_t) {
         table_insert<true>(tab, lgT, f, 1, smin, unweighted, meta, sl);
       });
+#if SLG_CTA_LIST_SORT
+      // as in the giant bin: survivors ranked in the list area while the
+      // table is cleared, each written straight to its place
+      __syncthreads();  // inserts done: the list is final
+      const int32_t nl = min(*sl.n, sl.cap);
+      if (emit && nl <= Cfg::kListSortMax) {  // uniform
+        if (threadIdx.x == 0) *s_base = reserve(a, e, nl, BIN);
+        unsigned long long *lk = reinterpret_cast<unsigned long long *>(sl.slot) + ((nl + 1) >> 1);
+        for (int32_t i = threadIdx.x; i < nl; i += NT) lk[i] = tab[sl.slot[i]] + 1ull;
+        __syncthreads();  // keys and base in place; every table and slot read done
+        clear_slots<NT>(tab, T);
+        if (threadIdx.x == 0) *sl.n = 0;
+        const long long base = *s_base;
+        if (base >= 0)
+          rank_keys<NT, false>(lk, nl, [&](int32_t r, unsigned long long x) {
+            put(a, base, r, e, (int32_t)(x >> 32), (int32_t)(uint32_t)x);
+          });
+        __syncthreads();  // keys and base read before the next row
+        continue;
+      }
+#endif
       total = table_collect_list<NT, Cfg::kQ>(tab, T, sl, emit, &at, &used);
     } else {
       cta_walk<NT, 4>(w, k0, k1, s_beg, s_pref, ws, [&](int32_t f, int32_t) {
