@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define SLG_ABI_VERSION 7
+#define SLG_ABI_VERSION 8
 
 /* Incidence of H as CSR + CSC (Section III: the hyperedge/vertex incidence
  * and its bipartite form).  All pointers are device pointers. */
@@ -503,6 +503,33 @@ int slg_last_stats(slg_stats *out);
  * density outside (0, 1].
  */
 int slg_set_core_params(int32_t tau_c, int32_t tau_r, float min_density);
+
+/*
+ * slg_graph -- one device hypergraph prepared for several calls.  Every call
+ * validates its input (offsets, id ranges, ascending rows and columns, CSR
+ * and CSC the same incidence) and maps each CSR incidence to its CSC
+ * position; a handle does both once, for both sides, and the builds and
+ * counts made through it skip them.  The caller's arrays must stay valid and
+ * unchanged while the handle lives.  Not a paper operation: a library
+ * service for inputs that stay on the device (several thresholds or sides of
+ * one hypergraph, served queries).
+ * slg_graph_create -- validates h (errors as slg_count) and keeps 2 x nnz
+ *   int32 of device memory for the maps; synchronises `stream`.
+ * slg_graph_count, slg_graph_build -- slg_count and slg_build on the
+ *   handle's hypergraph: the same arguments, flags, results and errors; a
+ *   relabelling flag makes the call map its renumbered side itself.  Calls
+ *   on one handle may run on several streams and host threads at once.
+ *   SLG_ERR_INVALID when the current device is not the handle's.
+ * slg_graph_destroy -- waits for the handle's stream and releases it.
+ */
+typedef struct slg_graph slg_graph;
+int slg_graph_create(const slg_hypergraph *h, slg_graph **graph, void *stream);
+int slg_graph_count(const slg_graph *graph, int32_t s, uint32_t flags, int64_t *n_pairs,
+                    void *stream);
+int slg_graph_build(const slg_graph *graph, int32_t s, uint32_t flags, int32_t *out_i,
+                    int32_t *out_j, int32_t *out_w, int64_t capacity, int64_t *n_pairs,
+                    void *stream);
+int slg_graph_destroy(slg_graph *graph);
 
 /* Returns the device memory that the library keeps for later calls on the
  * current device (its stream-ordered pool of working buffers) to the

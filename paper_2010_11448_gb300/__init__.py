@@ -25,7 +25,7 @@ __all__ = [
     "build_stream",
     "set_core_params", "SLG_TENSOR_CORE", "SLG_RELABEL_ASC", "SLG_RELABEL_DESC",
     "SLG_NO_PRUNE",
-    "Plan", "alloc_outputs",
+    "Plan", "Graph", "alloc_outputs",
     "library_path", "load",
     "SLG_DUAL", "SLG_UNWEIGHTED", "SLG_ALGO_BINNED", "SLG_ALGO_PLAIN",
     "SLG_ALGO_SPGEMM", "SlgError", "ABI_FUNCTIONS",
@@ -150,6 +150,11 @@ ABI_FUNCTIONS = {
     "slg_plan_info": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_float),
                                      ctypes.POINTER(ctypes.c_int32)]),
     "slg_plan_destroy": (ctypes.c_int, [_VP]),
+    "slg_graph_create": (ctypes.c_int, [_HP, ctypes.POINTER(ctypes.c_void_p), _VP]),
+    "slg_graph_count": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_uint32, _I64P, _VP]),
+    "slg_graph_build": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_uint32, _VP, _VP, _VP,
+                                       ctypes.c_int64, _I64P, _VP]),
+    "slg_graph_destroy": (ctypes.c_int, [_VP]),
     "slg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "slg_abi_version": (ctypes.c_int, []),
     "slg_last_error_where": (ctypes.c_int, []),
@@ -635,6 +640,69 @@ class _DeviceInt32:
     def __init__(self, ptr, n):
         self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<i4",
                                          "data": (ptr, False), "version": 3}
+
+
+class Graph:
+    """A device hypergraph prepared for several calls (slg_graph_*): the
+    input is validated and both sides' CSR->CSC maps are made once, in
+    ``Graph(h)``; ``count`` and ``build`` then take the same arguments as the
+    module-level functions (binned or plain algorithm, either side) and skip
+    that work.  ``close()`` (or the context manager) releases it; ``h`` must
+    stay alive and unchanged meanwhile."""
+
+    def __init__(self, h: DeviceHypergraph, stream=None):
+        self.h = h
+        self._g = ctypes.c_void_p()
+        rc = load().slg_graph_create(ctypes.byref(h.struct), ctypes.byref(self._g),
+                                     _stream(stream))
+        if rc != 0:
+            raise SlgError(rc, "slg_graph_create")
+
+    def count(self, s: int, dual=False, unweighted=False, algo="binned", stream=None,
+              tensor=False, prune=True) -> int:
+        n = ctypes.c_int64(0)
+        rc = load().slg_graph_count(self._g, int(s),
+                                    _flags(dual, unweighted, algo, tensor, None, prune),
+                                    ctypes.byref(n), _stream(stream))
+        if rc != 0:
+            raise SlgError(rc, "slg_graph_count")
+        return int(n.value)
+
+    def build(self, s: int, dual=False, unweighted=False, algo="binned", capacity=None,
+              out=None, stream=None, tensor=False, prune=True):
+        flags = _flags(dual, unweighted, algo, tensor, None, prune)
+        if out is None:
+            if capacity is None:
+                capacity = self.count(s, dual, unweighted, algo, stream, tensor, prune)
+            out = _outputs(capacity, unweighted, self.h.e_off.device)
+        oi, oj, ow = out
+        n = ctypes.c_int64(0)
+        rc = load().slg_graph_build(self._g, int(s), flags, oi.data_ptr(), oj.data_ptr(),
+                                    ow.data_ptr() if ow is not None else None,
+                                    int(oi.shape[0]), ctypes.byref(n), _stream(stream))
+        if rc != 0:
+            err = SlgError(rc, "slg_graph_build")
+            err.needed = int(n.value)
+            raise err
+        p = int(n.value)
+        return oi[:p], oj[:p], (ow[:p] if ow is not None else None)
+
+    def close(self):
+        if self._g:
+            load().slg_graph_destroy(self._g)
+            self._g = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Plan:

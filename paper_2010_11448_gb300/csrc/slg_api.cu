@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <memory>
 #include <mutex>
+#include <new>
 #include <vector>
 
 #include "slg_internal.cuh"
@@ -69,6 +70,27 @@ thread_local int t_profile = 0;
 thread_local int32_t t_tau_c = 64, t_tau_r = 32;
 thread_local Bins t_bins;
 thread_local float t_min_density = 0.02f;
+
+// Validation and the CSR->CSC maps of both sides of one device input, made
+// once for several builds on it (slg_build_host_many, slg_graph_*).  While
+// t_prep points to one, run() on the same input skips its own validation and
+// map.
+struct Prepared {
+  slg_hypergraph h{};
+  int32_t *map[2] = {nullptr, nullptr};  // side H, side H*
+};
+thread_local const Prepared *t_prep = nullptr;
+
+bool same_input(const slg_hypergraph &a, const slg_hypergraph &b) {
+  return a.n_edges == b.n_edges && a.n_vertices == b.n_vertices && a.nnz == b.nnz &&
+         a.e_off == b.e_off && a.e_idx == b.e_idx && a.v_off == b.v_off && a.v_idx == b.v_idx;
+}
+
+// t_prep for the lifetime of a scope
+struct PrepScope {
+  explicit PrepScope(const Prepared *p) { t_prep = p; }
+  ~PrepScope() { t_prep = nullptr; }
+};
 
 // Events of one profiled call: plan start, walk (kNumBins + 1), scan end,
 // gather start and end, relabel start and end, re-ordering start and end.
@@ -735,8 +757,12 @@ int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin
   Work &w = c.w;
   const int32_t ntiles = (int32_t)((nnz + 4095) / 4096);
   const int32_t ntiles64 = (c.rows + 4095) / 4096;
+  // a prepared input (validated, maps made): its map of this side is used
+  // as it is (read only; relabelling makes its own)
+  const Prepared *pp = (t_prep && !relabel && same_input(t_prep->h, *h)) ? t_prep : nullptr;
   SLG_TRY(pool.get(&w.meta, 1));
-  SLG_TRY(pool.get(&w.csr2csc, (size_t)nnz));
+  if (pp) w.csr2csc = pp->map[(flags & SLG_DUAL) ? 1 : 0];
+  else SLG_TRY(pool.get(&w.csr2csc, (size_t)nnz));
   SLG_TRY(pool.get(&w.qs, (size_t)nnz + 1));
   SLG_TRY(pool.get(&w.c_idx_s, (size_t)nnz * ((flags & SLG_TENSOR_CORE) ? 2 : 1) + 1));
   SLG_TRY(pool.get(&w.c_off_s, (size_t)c.sd.C + 1));
@@ -751,11 +777,14 @@ int run(const slg_hypergraph *h, int32_t smin, uint32_t flags, int32_t row_begin
   SLG_TRY(pool.get(&w.tile64, (size_t)ntiles64 + 1));
   SLG_TRY(cudaMemsetAsync(w.meta, 0, sizeof(Meta), st));
 
-  // Validation and the CSR->CSC map (a consistency check for every path).
+  // Validation and the CSR->CSC map (a consistency check for every path),
+  // unless the input was prepared.
   if (evs.on) cudaEventRecord(evs.ev[kEvPlan], st);
-  SLG_TRY(launch_validate(c.sd, w.meta, st));
-  SLG_TRY(launch_csr2csc(c.sd, w.csr2csc, w.meta, st));
-  c.launches += 3;
+  if (!pp) {
+    SLG_TRY(launch_validate(c.sd, w.meta, st));
+    SLG_TRY(launch_csr2csc(c.sd, w.csr2csc, w.meta, st));
+    c.launches += 3;
+  }
 
   // Degree-ordered relabelling: the rest of the call runs on a renumbered
   // copy of the side (built only from input that passed validation).
@@ -963,6 +992,37 @@ cudaError_t enqueue_plan(slg_plan *p, const Bins &bins, cudaStream_t st, int32_t
 
 }  // namespace
 namespace {
+
+// Validates the device input h as every call does and fills p with it and
+// both sides' CSR->CSC maps, written to map0 and map1 (device arrays of nnz
+// entries owned by the caller).  Synchronises `st`.
+int prepare(const slg_hypergraph *h, int32_t *map0, int32_t *map1, cudaStream_t st,
+            Prepared *p) {
+  int rc = check_args(h, 1, 0);
+  if (rc != SLG_OK) return rc;
+  const Side sd = side_of(h, 0);
+  Pool pool(st);
+  Meta *meta = nullptr;
+  SLG_TRY(pool.get(&meta, 1));
+  SLG_TRY(cudaMemsetAsync(meta, 0, sizeof(Meta), st));
+  SLG_TRY(launch_validate(sd, meta, st));
+  SLG_TRY(launch_csr2csc(sd, map0, meta, st));
+  Meta *mh = nullptr, *mv = nullptr;
+  SLG_TRY(thread_meta(&mh, &mv));
+  SLG_TRY(launch_meta_copy(meta, mv, st));
+  SLG_TRY(cudaStreamSynchronize(st));
+  if (mh->err) {
+    t_err_where = mh->err_where;
+    return mh->err;
+  }
+  // the input is valid: map0 is a permutation of [0, nnz)
+  SLG_TRY(launch_invert(map0, h->nnz, map1, st));
+  SLG_TRY(cudaStreamSynchronize(st));
+  p->h = *h;
+  p->map[0] = map0;
+  p->map[1] = map1;
+  return SLG_OK;
+}
 
 // Device copy of a host hypergraph, enqueued on `st` (buffers from `pool`).
 int upload(const slg_hypergraph *hh, Pool &pool, cudaStream_t st, slg_hypergraph *d) {
@@ -1201,6 +1261,17 @@ int slg_build_host_many(const slg_hypergraph *hh, slg_query *queries, int32_t co
   slg_hypergraph d;
   rc = upload(hh, pool, st, &d);
   if (rc != SLG_OK) return rc;
+  // validated and mapped once for every query of the call
+  Prepared prep;
+  int32_t *map0 = nullptr, *map1 = nullptr;
+  SLG_TRY(pool.get(&map0, (size_t)std::max<int64_t>(d.nnz, 1)));
+  SLG_TRY(pool.get(&map1, (size_t)std::max<int64_t>(d.nnz, 1)));
+  rc = prepare(&d, map0, map1, st, &prep);
+  if (rc != SLG_OK) {
+    for (int32_t k = 0; k < count; ++k) queries[k].status = rc;
+    return rc;
+  }
+  PrepScope prep_scope(&prep);
   int dev = 0;
   cudaStream_t cs = nullptr;
   cudaEvent_t done = nullptr;
@@ -1753,5 +1824,83 @@ extern "C" int slg_plan_destroy(slg_plan *p) {
   if (p->exec) cudaGraphExecDestroy(p->exec);
   if (p->graph) cudaGraphDestroy(p->graph);
   delete p;
+  return SLG_OK;
+}
+
+// ------------------------------------------------------------ graph handle --
+
+struct slg_graph {
+  slg::Prepared p;
+  int32_t *maps = nullptr;  // both sides' CSR->CSC maps (2 x nnz)
+  cudaStream_t st = nullptr;
+  int dev = 0;
+};
+
+extern "C" int slg_graph_create(const slg_hypergraph *h, slg_graph **graph, void *stream) {
+  if (!graph) return SLG_ERR_INVALID;
+  *graph = nullptr;
+  int rc = check_args(h, 1, 0);
+  if (rc != SLG_OK) return rc;
+  slg_graph *g = new (std::nothrow) slg_graph();
+  if (!g) return SLG_ERR_NOMEM;
+  g->st = (cudaStream_t)stream;
+  cudaGetDevice(&g->dev);
+  const size_t n = (size_t)std::max<int64_t>(h->nnz, 1);
+  cudaMemPool_t mem = lib_pool();
+  void *q = nullptr;
+  const cudaError_t e = mem ? cudaMallocFromPoolAsync(&q, 2 * n * sizeof(int32_t), mem, g->st)
+                            : cudaMallocAsync(&q, 2 * n * sizeof(int32_t), g->st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete g;
+    return status_of(e);
+  }
+  g->maps = static_cast<int32_t *>(q);
+  rc = prepare(h, g->maps, g->maps + n, g->st, &g->p);
+  if (rc != SLG_OK) {
+    cudaFreeAsync(g->maps, g->st);
+    cudaStreamSynchronize(g->st);
+    delete g;
+    return rc;
+  }
+  *graph = g;
+  return SLG_OK;
+}
+
+namespace {
+int graph_check(const slg_graph *g) {
+  if (!g) return SLG_ERR_INVALID;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return dev == g->dev ? SLG_OK : SLG_ERR_INVALID;
+}
+}  // namespace
+
+extern "C" int slg_graph_count(const slg_graph *g, int32_t s, uint32_t flags, int64_t *n_pairs,
+                               void *stream) {
+  const int rc = graph_check(g);
+  if (rc != SLG_OK) return rc;
+  PrepScope scope(&g->p);
+  return slg_count(&g->p.h, s, flags, n_pairs, stream);
+}
+
+extern "C" int slg_graph_build(const slg_graph *g, int32_t s, uint32_t flags, int32_t *out_i,
+                               int32_t *out_j, int32_t *out_w, int64_t capacity,
+                               int64_t *n_pairs, void *stream) {
+  const int rc = graph_check(g);
+  if (rc != SLG_OK) return rc;
+  PrepScope scope(&g->p);
+  return slg_build(&g->p.h, s, flags, out_i, out_j, out_w, capacity, n_pairs, stream);
+}
+
+extern "C" int slg_graph_destroy(slg_graph *g) {
+  if (!g) return SLG_OK;
+  cudaFreeAsync(g->maps, g->st);
+  const cudaError_t e = cudaStreamSynchronize(g->st);
+  delete g;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return SLG_ERR_CUDA;
+  }
   return SLG_OK;
 }

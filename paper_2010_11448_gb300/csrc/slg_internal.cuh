@@ -395,6 +395,8 @@ struct Work {
 
 cudaError_t launch_validate(const Side &s, Meta *meta, cudaStream_t st);
 cudaError_t launch_csr2csc(const Side &s, int32_t *csr2csc, Meta *meta, cudaStream_t st);
+// inv[map[k]] = k (k < n): a permutation's inverse.
+cudaError_t launch_invert(const int32_t *map, int64_t n, int32_t *inv, cudaStream_t st);
 cudaError_t launch_filter(const Side &s, int32_t smin, const Work &w, cudaStream_t st);
 cudaError_t launch_rows_work(const Side &s, int32_t smin, int32_t row_begin, int32_t row_end,
                              const Work &w, const CoreInfo &core, const Bins &bins,

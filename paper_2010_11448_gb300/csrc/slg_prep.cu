@@ -4,6 +4,8 @@
 // of every incidence (strict upper triangle, Section IV-C), and the binning of
 // rows by wedge work (the GPU counterpart of the load balancing of
 // Section IV-F).
+#include <algorithm>
+
 #include "slg_internal.cuh"
 
 namespace slg {
@@ -333,6 +335,21 @@ cudaError_t launch_validate(const Side &s, Meta *meta, cudaStream_t st) {
                                                           kWhereRowOffsets, kWhereRowIds);
   k_validate<<<grid_for(s.C, wpb, 65536), kValNT, 0, st>>>(s.c_off, s.c_idx, s.C, s.R, s.nnz, meta,
                                                           kWhereColOffsets, kWhereColIds);
+  return cudaGetLastError();
+}
+
+// inv[map[k]] = k for k < n: the CSR->CSC map of the dual side from that of
+// the primal side (the dual's CSR is the primal's CSC and vice versa).
+__global__ void k_invert(const int32_t *__restrict__ map, int64_t n, int32_t *__restrict__ inv) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t m = map[k];
+    if (m >= 0 && m < n) inv[m] = (int32_t)k;  // a validated map is a permutation
+  }
+}
+
+cudaError_t launch_invert(const int32_t *map, int64_t n, int32_t *inv, cudaStream_t st) {
+  if (n > 0) k_invert<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(map, n, inv);
   return cudaGetLastError();
 }
 

@@ -58,7 +58,7 @@ def test_binding_constants_match_header():
 def test_host_only_calls(lib):
     import paper_2010_11448_gb300 as slg
     L = slg.load()
-    assert L.slg_abi_version() == 7
+    assert L.slg_abi_version() == 8
     assert L.slg_strerror(2).decode().startswith("output capacity")
     # argument checks run on the host before any device work
     n = ctypes.c_int64(0)

@@ -502,3 +502,32 @@ def test_build_host_many_w16_overflow():
     assert res[0] == (6, 2) and res[1] == (0, 2) and res[2] == (0, 0)
     assert qs[1]["out_i"][:2].tolist() == [0, 2] and qs[1]["out_j"][:2].tolist() == [1, 3]
     assert qs[1]["out_w"][:2].tolist() == [70_000, 2]
+
+
+def test_graph_handle(medium):
+    # slg_graph: validated and mapped once; builds and counts through it on
+    # both sides equal the oracle and skip the three validation/map kernels
+    h, dh = medium
+    with slg.Graph(dh) as g:
+        for dual in (False, True):
+            for s in (2, 4):
+                want = want_lg(h, s, dual)
+                assert g.count(s, dual) == want.shape[0]
+                got = g.build(s, dual=dual)
+                launches_handle = slg.last_stats()["kernel_launches"]
+                assert np.array_equal(as_np(got), want), (dual, s)
+                slg.build(dh, s, dual=dual)
+                assert slg.last_stats()["kernel_launches"] == launches_handle + 3
+            assert np.array_equal(as_np(g.build(3, dual=dual, algo="plain")), want_lg(h, 3, dual))
+
+
+def test_graph_handle_rejects_bad_input():
+    # CSR and CSC of different incidences: the handle is refused, as every
+    # build on that input would be
+    a = hg.from_rows([[0, 1], [1, 2]], 3)
+    b = hg.from_rows([[0, 1], [0, 2]], 3)
+    bad = slg.DeviceHypergraph(a.m, a.n, *[torch.from_numpy(np.ascontiguousarray(x, np.int32)).cuda()
+                                          for x in (a.e_off, a.e_idx, b.v_off, b.v_idx)])
+    with pytest.raises(slg.SlgError) as exc:
+        slg.Graph(bad)
+    assert exc.value.status == 1
