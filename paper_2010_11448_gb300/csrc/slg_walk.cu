@@ -1372,9 +1372,16 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
   }
 }
 
+// The first walk also copies the row's far ends (in flattened wedge order) to
+// the CTA's part of the giant bin's scratch (free while this kernel runs:
+// the giant bin runs after it), so that the second pass reads them in order
+// instead of walking the tails again.  buf_stride: ints per CTA (0: none).
+#ifndef SLG_SP_GBUF
+#define SLG_SP_GBUF 1
+#endif
 __global__ __launch_bounds__(kSpNT, SLG_SP_MINB) void k_walk_sparse(
     Walk w, const int32_t *__restrict__ rows, EmitArgs a, int32_t *__restrict__ giant_rows,
-    int32_t list_len) {
+    int32_t list_len, int32_t *__restrict__ buf, long long buf_stride) {
   Meta *meta = a.meta;
   if (meta->err) return;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1421,6 +1428,10 @@ __global__ __launch_bounds__(kSpNT, SLG_SP_MINB) void k_walk_sparse(
     const int32_t work = a.row_work[e - a.row_begin];
     const int32_t k0 = w.r_off[e], k1 = w.r_off[e + 1];
     const bool cached = work <= kSpCache;
+    // the far ends kept in global scratch for the second pass (uniform)
+    int32_t *gbuf = (SLG_SP_GBUF && !cached && (long long)work <= buf_stride)
+                        ? buf + (long long)blockIdx.x * buf_stride
+                        : nullptr;
     int lgb, lgt;
     sp_sizes(work, &lgb, &lgt);
     const int32_t T = 1 << lgt;
@@ -1436,6 +1447,7 @@ __global__ __launch_bounds__(kSpNT, SLG_SP_MINB) void k_walk_sparse(
 #pragma unroll
           for (int g = 0; g < kSpG; ++g) {
             if (cached && f[g] >= 0) cache[i0 + 32 * g] = f[g];
+            if (gbuf && f[g] >= 0) gbuf[i0 + 32 * g] = f[g];
             const uint32_t h = sp_h1(f[g], lgb);
             m[g] = f[g] >= 0 ? 1u << (h & 31) : 0u;
             old[g] = f[g] >= 0 ? atomicOr(filt + (h >> 5), m[g]) : 0u;
@@ -1474,7 +1486,40 @@ __global__ __launch_bounds__(kSpNT, SLG_SP_MINB) void k_walk_sparse(
       continue;
     }
     // 2. exact counts of the candidates
-    if (cached) {
+    // (the deferred slow path, as in the walk below)
+    auto count_step = [&](const int32_t(&f)[kSpG]) {
+      uint32_t word[kSpG], bit[kSpG];
+#pragma unroll
+      for (int g = 0; g < kSpG; ++g) {  // the candidate filter, loads in flight together
+        const uint32_t c = sp_h2(f[g], lgb);
+        bit[g] = 1u << (c & 31);
+        word[g] = f[g] >= 0 ? cand[c >> 5] : 0u;
+      }
+      int32_t pend[kSpG] = {};
+      int np = 0;
+#pragma unroll
+      for (int g = 0; g < kSpG; ++g) pend_push(pend, np, (word[g] & bit[g]) != 0, f[g], g);
+#pragma unroll
+      for (int q = 0; q < kSpG; ++q) {
+        if (!__any_sync(0xffffffffu, q < np)) break;
+        if (q < np) sp_count_listed(tab, pend[q], smin, unweighted, lgt);
+      }
+    };
+    if (gbuf) {
+      // warp-uniform steps over the copy, 32 consecutive far ends per load
+      const int32_t lane = tid & 31;
+      for (int32_t b0 = (tid >> 5) * 32 * kSpG; b0 < work; b0 += kSpNT * kSpG) {
+        int32_t f[kSpG];
+#pragma unroll
+        for (int g = 0; g < kSpG; ++g) {
+          const int32_t i = b0 + 32 * g + lane;
+          f[g] = i < work ? gbuf[i] : -1;
+        }
+        count_step(f);
+      }
+      __syncthreads();  // every read of the copy done
+      l2_discard(gbuf, work);
+    } else if (cached) {
       for (int32_t i = tid; i < work; i += kSpNT)
         sp_count(tab, cand, cache[i], smin, unweighted, lgb, lgt);
     } else {
@@ -1626,8 +1671,15 @@ cudaError_t launch_walk(const WalkLaunch &L, cudaStream_t st, int32_t *launches,
   if (ev) cudaEventRecord(ev[3], st);
   // the sparse bin before the giant bin: a sparse row whose candidates
   // overflow its table is appended to the giant bin's list
+  // the sparse CTAs share the giant bin's scratch out (it holds at least
+  // 4 x max(giant, sparse row work) ints per giant CTA)
+  const long long buf_stride =
+      L.giant_scratch ? (L.giant_stride * (long long)(o.sms * o.g_blocks) /
+                         (long long)(o.sms * o.sp_blocks)) & ~31ll
+                      : 0;
   k_walk_sparse<<<o.sms * o.sp_blocks, kSpNT, sparse_smem(), st>>>(
-      L.w, lists + 4 * stride, L.a, const_cast<int32_t *>(lists) + 3 * stride, (int32_t)stride);
+      L.w, lists + 4 * stride, L.a, const_cast<int32_t *>(lists) + 3 * stride, (int32_t)stride,
+      L.giant_scratch, buf_stride);
   ++n;
   if (ev) cudaEventRecord(ev[4], st);
   if (L.giant_scratch) {
