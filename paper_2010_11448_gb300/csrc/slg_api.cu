@@ -1701,7 +1701,8 @@ extern "C" int slg_plan_create(const slg_hypergraph *hs, const int32_t *s, int32
                         Bins{128, 1024, 4096, 0},
                         Bins{128, 1024, 2048, 16384, 2048},
                         Bins{128, 1024, 4096, 16384, 4096, 4},
-                        Bins{128, 1024, 4096, 16384, 4096, 16}};
+                        Bins{128, 1024, 4096, 16384, 4096, 16},
+                        Bins{128, 1024, 4096, 16384, 4096, 8}};
   cudaEvent_t t0, t1;
   SLG_TRY(cudaEventCreate(&t0));
   SLG_TRY(cudaEventCreate(&t1));

@@ -346,7 +346,7 @@ __device__ __forceinline__ int32_t s_of(const int32_t *row_s, int32_t smin, int3
 #define SLG_SPARSE_MAX_WORK 16384
 #endif
 #ifndef SLG_BLOOM_MIN_WORK
-#define SLG_BLOOM_MIN_WORK 4096
+#define SLG_BLOOM_MIN_WORK 1024
 #endif
 // `dense`: a row with at least one wedge per `dense` ids of its far ends'
 // span is dense (the giant bin counts it in dense windows).
