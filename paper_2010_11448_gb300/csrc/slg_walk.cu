@@ -802,13 +802,15 @@ constexpr int kGiantG = 6;  // wedges per thread per step of the giant bin's wal
 static_assert(kGiantDirectMax <= kGiantTMax && kGiantDirectMax / 2 <= kGiantList,
               "a direct row fits the table and the survivor list");
 constexpr int kGiantQ = kGiantList / kGiantNT;
+static_assert(kNSB % kGiantNT == 0 && kGiantTMax % kGiantNT == 0 && kGiantList % kGiantNT == 0,
+              "giant bin geometry: whole sub-ranges, slots and list entries per thread");
 // Survivor sets of up to this many keys are ordered in the survivor-list
 // area (kGiantList ints = kGiantList / 2 keys): the keys start past the
 // slot indices (ceil(n / 2) keys) and their runs take 32 ceil(n / 32).
 #ifndef SLG_GIANT_LIST_SORT
 #define SLG_GIANT_LIST_SORT 1
 #endif
-constexpr int32_t kGiantListSortMax = 1024;
+constexpr int32_t kGiantListSortMax = kGiantList / 4;
 static_assert((kGiantListSortMax + 1) / 2 + 32 * ((kGiantListSortMax + 31) / 32) <=
                   kGiantList / 2,
               "the list area holds the runs of kGiantListSortMax keys");
