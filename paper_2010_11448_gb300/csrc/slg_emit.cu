@@ -71,6 +71,7 @@ __global__ __launch_bounds__(kNT) void k_rowscan_apply(const int32_t *__restrict
 }
 
 constexpr int kGatherRows = 256;
+constexpr int kGatherQ = 4;  // positions per thread whose loads are in flight together
 
 // A block owns kGatherRows consecutive rows and copies their staged pairs to
 // the output range [row_ptr[r0], row_ptr[r0 + rows)), each thread finding its
@@ -94,21 +95,51 @@ __global__ __launch_bounds__(kNT) void k_gather(int32_t row_begin, int32_t rows,
   for (int i = threadIdx.x; i < nr; i += kNT) s_sp[i] = stage_pos[r0 + i];
   __syncthreads();
   const long long p1 = s_ptr[nr];
-  for (long long p = s_ptr[0] + threadIdx.x; p < p1; p += kNT) {
-    int lo = 0, hi = nr;  // s_ptr[lo] <= p < s_ptr[hi]
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (s_ptr[mid] <= p) lo = mid;
-      else hi = mid;
+  // A thread's positions ascend, so its row index only moves forward: the
+  // next row is searched for only when p has left the current one, and the
+  // loads of kGatherQ positions are issued before their stores.
+  int lo = 0;  // s_ptr[lo] <= p for every p still to come
+  for (long long p0 = s_ptr[0] + threadIdx.x; p0 < p1; p0 += (long long)kGatherQ * kNT) {
+    long long src[kGatherQ];
+    int row[kGatherQ];
+#pragma unroll
+    for (int q = 0; q < kGatherQ; ++q) {
+      const long long p = p0 + (long long)q * kNT;
+      src[q] = -1;
+      row[q] = lo;
+      if (p < p1) {
+        if (s_ptr[lo + 1] <= p) {  // past the row: binary search in (lo, nr)
+          int a = lo + 1, hi = nr;  // s_ptr[a] <= p < s_ptr[hi]
+          while (hi - a > 1) {
+            const int mid = (a + hi) >> 1;
+            if (s_ptr[mid] <= p) a = mid;
+            else hi = mid;
+          }
+          lo = a;
+        }
+        row[q] = lo;
+        src[q] = s_sp[lo] < 0 ? -2 : s_sp[lo] + (p - s_ptr[lo]);
+      }
     }
-    const long long src = s_sp[lo] + (p - s_ptr[lo]);
-    if (s_sp[lo] < 0 || src >= stage_cap || p >= out_cap) {  // more pairs than counted
-      raise_error(meta, SLG_ERR_INVALID, kWhereStage);
-      continue;
+    int32_t vj[kGatherQ], vw[kGatherQ];
+#pragma unroll
+    for (int q = 0; q < kGatherQ; ++q) {
+      const bool ok = src[q] >= 0 && src[q] < stage_cap;
+      vj[q] = ok ? stage_j[src[q]] : 0;
+      vw[q] = ok && !unweighted ? stage_w[src[q]] : 0;
     }
-    if (out_i) out_i[p] = row_begin + r0 + lo;  // null: compressed row form
-    out_j[p] = stage_j[src];
-    if (!unweighted) out_w[p] = stage_w[src];
+#pragma unroll
+    for (int q = 0; q < kGatherQ; ++q) {
+      const long long p = p0 + (long long)q * kNT;
+      if (p >= p1) continue;
+      if (src[q] < 0 || src[q] >= stage_cap || p >= out_cap) {  // more pairs than counted
+        raise_error(meta, SLG_ERR_INVALID, kWhereStage);
+        continue;
+      }
+      if (out_i) out_i[p] = row_begin + r0 + row[q];  // null: compressed row form
+      out_j[p] = vj[q];
+      if (!unweighted) out_w[p] = vw[q];
+    }
   }
 }
 
