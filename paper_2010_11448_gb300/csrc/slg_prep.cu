@@ -193,6 +193,10 @@ __global__ __launch_bounds__(kRowsNT) void k_rows_work(Side s, int32_t smin, int
                                                        Meta *meta) {
   if (meta->err) return;
   __shared__ int32_t s_work[kRowsPerBlock];
+  // block maxima of the row work (all rows, giant-bin rows, sparse-bin rows):
+  // one global atomicMax each per block instead of one per row
+  __shared__ int32_t s_max[3];
+  __shared__ int32_t s_act;  // active rows (size >= s) of the block
   __shared__ int32_t s_cnt[kNumBins], s_base[kNumBins];
   __shared__ int32_t s_hcnt[2], s_hbase[2];  // giant / sparse rows above kGiantHugeWork
   __shared__ unsigned long long s_w[kNumBins], s_k[kNumBins];
@@ -204,13 +208,17 @@ __global__ __launch_bounds__(kRowsNT) void k_rows_work(Side s, int32_t smin, int
     s_k[threadIdx.x] = 0;
   }
   if (threadIdx.x < 2) s_hcnt[threadIdx.x] = 0;
+  if (threadIdx.x < 3) s_max[threadIdx.x] = 0;
+  if (threadIdx.x == 0) s_act = 0;
+  __syncthreads();
   for (int i = warp; i < kRowsPerBlock; i += kRowsNT / 32) {
     const int32_t e = r0 + i;
     int32_t work = 0;
     if (e < row_end) {
       const int32_t lo = s.r_off[e], hi = s.r_off[e + 1];
       const bool core_row = core.row_rank && core.row_rank[e + 1] != core.row_rank[e];
-      if (hi - lo >= s_of(s.row_s, smin, e)) {
+      const bool active = hi - lo >= s_of(s.row_s, smin, e);
+      if (active) {
         for (int32_t k = lo + lane; k < hi; k += 32) {
           const int32_t v = s.r_idx[k];
           int32_t tb, te;
@@ -241,7 +249,8 @@ __global__ __launch_bounds__(kRowsNT) void k_rows_work(Side s, int32_t smin, int
         n_e[e - row_begin] = 0;
         stage_pos[e - row_begin] = -1;
         row_work[e - row_begin] = work;
-        if (work) atomicMax(&meta->max_row_work, work);
+        if (work) atomicMax(&s_max[0], work);
+        if (active) atomicAdd(&s_act, 1);
       }
     }
     if (lane == 0) {
@@ -271,8 +280,8 @@ __global__ __launch_bounds__(kRowsNT) void k_rows_work(Side s, int32_t smin, int
           (my_bin != kBinGiant ||
            (long long)my_work * bins.dense < (long long)((s.row_fhi ? s.row_fhi[e] : s.R) - 1 - e)))
         my_bin = kBinSparse;
-      if (my_bin == kBinGiant) atomicMax(&meta->max_giant_work, my_work);
-      if (my_bin == kBinSparse) atomicMax(&meta->max_sparse_work, my_work);
+      if (my_bin == kBinGiant) atomicMax(&s_max[1], my_work);
+      if (my_bin == kBinSparse) atomicMax(&s_max[2], my_work);
       huge = (my_bin == kBinGiant || my_bin == kBinSparse) && my_work > kGiantHugeWork;
       my_slot = huge ? atomicAdd(&s_hcnt[my_bin == kBinSparse], 1) : atomicAdd(&s_cnt[my_bin], 1);
       atomicAdd(&s_w[my_bin], (unsigned long long)my_work);
@@ -302,15 +311,13 @@ __global__ __launch_bounds__(kRowsNT) void k_rows_work(Side s, int32_t smin, int
       atomicAdd(&meta->incid_bin[b], s_k[b]);
     }
   }
-  if (threadIdx.x == kNumBins) {
-    int act = 0;
-    for (int i = 0; i < kRowsPerBlock; ++i) {
-      const int32_t e = r0 + i;
-      if (e < row_end && s.r_off[e + 1] - s.r_off[e] >= s_of(s.row_s, smin, e)) ++act;
-    }
-    if (act) atomicAdd(&meta->active, (unsigned long long)act);
-  }
+  if (threadIdx.x == kNumBins && s_act) atomicAdd(&meta->active, (unsigned long long)s_act);
   __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_max[0]) atomicMax(&meta->max_row_work, s_max[0]);
+    if (s_max[1]) atomicMax(&meta->max_giant_work, s_max[1]);
+    if (s_max[2]) atomicMax(&meta->max_sparse_work, s_max[2]);
+  }
   if (my_bin >= 0) {
     const int64_t len = row_end - row_begin;
     int64_t pos = s_base[my_bin] + my_slot;
