@@ -520,7 +520,8 @@ int slg_set_core_params(int32_t tau_c, int32_t tau_r, float min_density);
  *   relabelling flag makes the call map its renumbered side itself.  Calls
  *   on one handle may run on several streams and host threads at once.
  *   SLG_ERR_INVALID when the current device is not the handle's.
- * slg_graph_destroy -- waits for the handle's stream and releases it.
+ * slg_graph_destroy -- releases the handle's memory on the stream given to
+ *   slg_graph_create (which must still exist) and waits for that stream.
  */
 typedef struct slg_graph slg_graph;
 int slg_graph_create(const slg_hypergraph *h, slg_graph **graph, void *stream);
