@@ -31,7 +31,10 @@ enum Bin : int {
 // Upper bounds on a row's wedge count for each non-giant bin.  The hash tables
 // hold twice the bound, so a row can never fill its table (distinct
 // neighbours <= wedges).
-constexpr int32_t kWarpMaxWork = 128;
+#ifndef SLG_WARP_MAX_WORK
+#define SLG_WARP_MAX_WORK 128
+#endif
+constexpr int32_t kWarpMaxWork = SLG_WARP_MAX_WORK;
 constexpr int32_t kCtaSMaxWork = 1024;
 constexpr int32_t kCtaLMaxWork = 4096;
 // Giant rows above this work are handed out first (largest-first order
