@@ -484,8 +484,10 @@ typedef struct slg_stats {
   float ms_relabel;        /* SLG_RELABEL_*: building the renumbered side */
   float ms_order;          /* SLG_RELABEL_*: caller ids and (i, j) order */
   int64_t sparse_cycles[5]; /* sparse bin, SM clock cycles summed over CTAs:
-                               row set-up, first walk, second walk, collect
-                               and order the survivors, emit and clear */
+                               row set-up, first walk, second pass (over the
+                               copy of the far ends the first walk made),
+                               collect and order the survivors, emit and
+                               clear */
   float ms_tile;           /* the tensor-core tile kernel of the dense core
                               (SLG_TENSOR_CORE builds, slg_tile_overlap) */
 } slg_stats;

@@ -594,7 +594,7 @@ __global__ __launch_bounds__(NT, MINB) void k_walk_cta(Walk w, const int32_t *__
 // every far end of such a row occurs once (on the Chung-Lu workloads about
 // 96 % of the wedges of these rows are the only wedge to their far end), and
 // a far end with a single wedge can never reach s >= 2.  The row is counted
-// in two walks with little shared memory, so that several rows are in
+// in two passes with little shared memory, so that several rows are in
 // flight on each SM (the walk's far-end gathers are latency-bound: a row at
 // a time per SM leaves the memory system idle):
 //   1. every wedge sets its far end's bit in a one-hash Bloom filter (one
@@ -603,14 +603,15 @@ __global__ __launch_bounds__(NT, MINB) void k_walk_cta(Walk w, const int32_t *__
 //      marked in a second filter.  Every f with two or more wedges becomes
 //      a candidate (its second wedge finds the bit set); so may a few
 //      single-wedge f whose bit another f had set;
-//   2. a second walk counts, exactly, every wedge whose far end is a
+//   2. a second pass counts, exactly, every wedge whose far end is a
 //      candidate (the second filter screens out almost all others before
-//      the table is probed).  The count of f is then |e ∩ f|.
-// The candidates with count >= s are sorted and emitted.  A row of at most
-// kSpCache wedges keeps its far ends in shared memory during the first walk
-// and reads them from there in the second.  A row whose candidates overflow
-// the table (a probe sequence longer than kSpMaxProbe) is handed to the
-// giant bin, which runs after this one.
+//      the table is probed).  The count of f is then |e ∩ f|.  It reads the
+//      row's far ends from a copy the first walk wrote to global scratch
+//      (or, for a row of at most kSpCache wedges, to shared memory), or
+//      walks the tails again when there is no room for the copy.
+// The candidates with count >= s are sorted and emitted.  A row whose
+// candidates overflow the table (a probe sequence longer than kSpMaxProbe)
+// is handed to the giant bin, which runs after this one.
 
 #ifndef SLG_SP_NT
 #define SLG_SP_NT 256
@@ -1587,7 +1588,7 @@ __global__ __launch_bounds__(kSpNT, SLG_SP_MINB) void k_walk_sparse(
         const int32_t f = (int32_t)(x >> 32), c = (int32_t)(uint32_t)x;
         put(a, base, i, e, f, c);
       }
-    clear_filters(lgb);  // nothing reads the filters after the second walk
+    clear_filters(lgb);  // nothing reads the filters after the second pass
     table_reset_front<kSpNT>(tab, used);
     cyc[4] += clock64() - t0;
   }
