@@ -3,6 +3,7 @@
 // kernels, and the single device->host read of the pair count.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <memory>
@@ -538,7 +539,10 @@ int run_binned(Call &c, int64_t *result) {
     } else {
       // Staging too small: walk again, writing straight to the output.
       SLG_TRY(cudaMemsetAsync(&w.meta->giant_ticket, 0, sizeof(unsigned int), c.st));
-      SLG_TRY(cudaMemsetAsync(&w.meta->sparse_ticket, 0, sizeof(unsigned int), c.st));
+      static_assert(offsetof(Meta, sparse_ticket_rest) ==
+                        offsetof(Meta, sparse_ticket) + sizeof(unsigned int),
+                    "the two sparse ticket counters are cleared together");
+      SLG_TRY(cudaMemsetAsync(&w.meta->sparse_ticket, 0, 2 * sizeof(unsigned int), c.st));
       // back to the planned giant list: the sparse bin hands the same rows
       // over again
       SLG_TRY(cudaMemcpyAsync(&w.meta->rows_bin[kBinGiant], &giant_rows0, sizeof(giant_rows0),

@@ -43,6 +43,14 @@ constexpr int32_t kCtaLMaxWork = 4096;
 #define SLG_GIANT_HUGE_WORK 32768
 #endif
 constexpr int32_t kGiantHugeWork = SLG_GIANT_HUGE_WORK;
+// Sparse rows above this work are handed out first, to the sparse kernel
+// with the larger candidate table; the others go to the one with the smaller
+// table and one more CTA per SM (0: a single sparse kernel, and no sparse
+// row is handed out first).
+#ifndef SLG_SP_BIG_WORK
+#define SLG_SP_BIG_WORK 8192
+#endif
+constexpr int32_t kSparseBigWork = SLG_SP_BIG_WORK > 0 ? SLG_SP_BIG_WORK : kGiantHugeWork;
 // A row is dense when it has at least one wedge per this many ids of its far
 // ends' span (swept: 8 best for the giant bin's dense windows).
 #ifndef SLG_DENSE_RATIO
@@ -67,6 +75,7 @@ struct Meta {
   unsigned int giant_huge;             // giant rows above kGiantHugeWork (front of the list)
   unsigned int giant_rest;             // the other giant rows (back of the list)
   unsigned int sparse_ticket;          // the same three for the sparse bin
+  unsigned int sparse_ticket_rest;     // the small-table sparse kernel's own tickets
   unsigned int sparse_huge;
   unsigned int sparse_rest;
   int32_t max_sparse_work;             // largest work of a sparse-bin row

@@ -198,7 +198,7 @@ __global__ __launch_bounds__(kRowsNT) void k_rows_work(Side s, int32_t smin, int
   __shared__ int32_t s_max[3];
   __shared__ int32_t s_act;  // active rows (size >= s) of the block
   __shared__ int32_t s_cnt[kNumBins], s_base[kNumBins];
-  __shared__ int32_t s_hcnt[2], s_hbase[2];  // giant / sparse rows above kGiantHugeWork
+  __shared__ int32_t s_hcnt[2], s_hbase[2];  // giant / sparse rows handed out first
   __shared__ unsigned long long s_w[kNumBins], s_k[kNumBins];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int32_t r0 = row_begin + blockIdx.x * kRowsPerBlock;
@@ -282,7 +282,8 @@ __global__ __launch_bounds__(kRowsNT) void k_rows_work(Side s, int32_t smin, int
         my_bin = kBinSparse;
       if (my_bin == kBinGiant) atomicMax(&s_max[1], my_work);
       if (my_bin == kBinSparse) atomicMax(&s_max[2], my_work);
-      huge = (my_bin == kBinGiant || my_bin == kBinSparse) && my_work > kGiantHugeWork;
+      huge = (my_bin == kBinGiant && my_work > kGiantHugeWork) ||
+             (my_bin == kBinSparse && my_work > kSparseBigWork);
       my_slot = huge ? atomicAdd(&s_hcnt[my_bin == kBinSparse], 1) : atomicAdd(&s_cnt[my_bin], 1);
       atomicAdd(&s_w[my_bin], (unsigned long long)my_work);
       atomicAdd(&s_k[my_bin], (unsigned long long)(s.r_off[e + 1] - s.r_off[e]));

@@ -18,6 +18,7 @@
 // Output modes: COUNT (pairs per row only), STAGE (each row's sorted pairs
 // are appended to a staging area at an atomically reserved offset) and
 // DIRECT (written to their final place, row_ptr known).
+#include <algorithm>
 #include <mutex>
 #include <type_traits>
 
@@ -612,6 +613,12 @@ __global__ __launch_bounds__(NT, MINB) void k_walk_cta(Walk w, const int32_t *__
 // The candidates with count >= s are sorted and emitted.  A row whose
 // candidates overflow the table (a probe sequence longer than kSpMaxProbe)
 // is handed to the giant bin, which runs after this one.
+// Two instances of the kernel share the bin: rows above kSparseBigWork go
+// to one with a 2^SLG_SP_LGT-slot table, the rest to one with a
+// 2^SLG_SP_SMALL_LGT-slot table, whose smaller shared memory leaves room for
+// one more resident CTA per SM.  Rows of up to 8192 wedges seldom have more
+// candidates or survivors than the smaller table holds (the overflow would
+// send them to the giant bin); rows of up to 16384 do.
 
 #ifndef SLG_SP_NT
 #define SLG_SP_NT 256
@@ -628,6 +635,12 @@ __global__ __launch_bounds__(NT, MINB) void k_walk_cta(Walk w, const int32_t *__
 #ifndef SLG_SP_MINB
 #define SLG_SP_MINB 4
 #endif
+#ifndef SLG_SP_SMALL_LGT
+#define SLG_SP_SMALL_LGT 11
+#endif
+#ifndef SLG_SP_SMALL_MINB
+#define SLG_SP_SMALL_MINB 5
+#endif
 #ifndef SLG_SP_G
 #define SLG_SP_G 6
 #endif
@@ -638,20 +651,20 @@ constexpr int kSpNT = SLG_SP_NT;
 constexpr int kSpLogB = SLG_SP_LOGB;          // Bloom filter bits (log2)
 constexpr int kSpWords = 1 << (kSpLogB - 5);
 constexpr int kSpCWords = kSpWords / 4;       // candidate filter words
-constexpr int kSpLgT = SLG_SP_LGT;
-constexpr int kSpT = 1 << kSpLgT;             // candidate table slots
+constexpr int kSpLgT = SLG_SP_LGT;            // candidate table slots (log2)
+constexpr int kSpSmallLgT = SLG_SP_SMALL_LGT;  // the same, rows up to kSparseBigWork
 constexpr int kSpCache = SLG_SP_CACHE;        // far ends kept of a small row
 constexpr int kSpMaxProbe = 32;
 constexpr int kSpG = SLG_SP_G;                // wedges per thread per walk step
-constexpr int kSpSPT = kSpT / kSpNT;          // table slots per thread
-static_assert(kSpSPT >= 1 && kSpWords % (4 * kSpNT) == 0 && kSpCWords % 4 == 0,
+static_assert((1 << kSpSmallLgT) >= kSpNT && kSpSmallLgT <= kSpLgT &&
+                  kSpWords % (4 * kSpNT) == 0 && kSpCWords % 4 == 0,
               "sparse bin geometry");
 
 // [s_base 8][s_ovf 4][s_row 4][pad 16][filter kSpWords x 4]
-// [candidate filter kSpCWords x 4][table kSpT x 8][cache kSpCache x 4]
+// [candidate filter kSpCWords x 4][table 2^lgt x 8][cache kSpCache x 4]
 // [s_beg NT][s_pref NT+1][ws NT/32+1]
-constexpr size_t sparse_smem() {
-  return 32 + (size_t)kSpWords * 4 + (size_t)kSpCWords * 4 + (size_t)kSpT * 8 +
+constexpr size_t sparse_smem(int lgt) {
+  return 32 + (size_t)kSpWords * 4 + (size_t)kSpCWords * 4 + ((size_t)8 << lgt) +
          (size_t)kSpCache * 4 + (size_t)(2 * kSpNT + 1 + kSpNT / 32 + 1) * 4;
 }
 
@@ -670,11 +683,12 @@ __device__ __forceinline__ uint32_t sp_ht(int32_t f, int lgt) {  // candidate ta
 // Per-row sizes: a filter of >= 32 bits per wedge (so that a single-wedge
 // far end finds its bit set by another with probability below 1/64 on
 // average) and a table of >= one slot per wedge (every candidate has two
-// wedges or is such a collision), within the shared-memory maxima.
-__device__ __forceinline__ void sp_sizes(int32_t work, int *lgb, int *lgt) {
+// wedges or is such a collision), within the shared-memory maxima (a table
+// of at most 2^max_lgt slots).
+__device__ __forceinline__ void sp_sizes(int32_t work, int max_lgt, int *lgb, int *lgt) {
   const int lw = ceil_log2(work > 1 ? work : 2);
   *lgb = min(max(lw + 5, 12), kSpLogB);
-  *lgt = min(max(lw, 7), kSpLgT);
+  *lgt = min(max(lw, 7), max_lgt);
 }
 
 // Pass 1: f is a candidate (its filter bit was already set).  Claims f's
@@ -1382,9 +1396,14 @@ __global__ __launch_bounds__(kGiantNT, SLG_GIANT_MINB) void k_walk_giant(Walk w,
 #ifndef SLG_SP_GBUF
 #define SLG_SP_GBUF 1
 #endif
-__global__ __launch_bounds__(kSpNT, SLG_SP_MINB) void k_walk_sparse(
+// part: 0 every row of the bin, 1 the rows handed out first (the front of
+// the list), 2 the others (the back of the list, on their own ticket).
+template <int LGT, int MINB>
+__global__ __launch_bounds__(kSpNT, MINB) void k_walk_sparse(
     Walk w, const int32_t *__restrict__ rows, EmitArgs a, int32_t *__restrict__ giant_rows,
-    int32_t list_len, int32_t *__restrict__ buf, long long buf_stride) {
+    int32_t list_len, int32_t *__restrict__ buf, long long buf_stride, int part) {
+  constexpr int kT = 1 << LGT;        // candidate table slots
+  constexpr int kSPT = kT / kSpNT;    // table slots per thread
   Meta *meta = a.meta;
   if (meta->err) return;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1394,7 +1413,7 @@ __global__ __launch_bounds__(kSpNT, SLG_SP_MINB) void k_walk_sparse(
   uint32_t *filt = reinterpret_cast<uint32_t *>(smem + 32);
   uint32_t *cand = filt + kSpWords;
   unsigned long long *tab = reinterpret_cast<unsigned long long *>(cand + kSpCWords);
-  int32_t *cache = reinterpret_cast<int32_t *>(tab + kSpT);
+  int32_t *cache = reinterpret_cast<int32_t *>(tab + kT);
   int32_t *s_beg = cache + kSpCache;
   int32_t *s_pref = s_beg + kSpNT;
   int32_t *ws = s_pref + kSpNT + 1;
@@ -1408,9 +1427,12 @@ __global__ __launch_bounds__(kSpNT, SLG_SP_MINB) void k_walk_sparse(
     for (int i = tid; i < (1 << (lgb - 9)); i += kSpNT) c4[i] = make_uint4(0, 0, 0, 0);
   };
   clear_filters(kSpLogB);
-  for (int i = tid; i < kSpT; i += kSpNT) tab[i] = kEmpty64;
+  for (int i = tid; i < kT; i += kSpNT) tab[i] = kEmpty64;
   const unsigned nrows = (unsigned)meta->rows_bin[kBinSparse];
   const unsigned nhuge = meta->sparse_huge;
+  unsigned *ticket = part == 2 ? &meta->sparse_ticket_rest : &meta->sparse_ticket;
+  const unsigned t_first = part == 2 ? nhuge : 0u;
+  const unsigned t_end = part == 1 ? nhuge : nrows;
   const bool unweighted = a.unweighted != 0;
   const bool emit = a.mode != kCount;
   // SM cycles of the CTA's first thread: row set-up, first walk, second
@@ -1420,9 +1442,9 @@ __global__ __launch_bounds__(kSpNT, SLG_SP_MINB) void k_walk_sparse(
     long long t0 = clock64();
     __syncthreads();  // the previous row's clears done
     if (tid == 0) {
-      const unsigned t = atomicAdd(&meta->sparse_ticket, 1u);
+      const unsigned t = t_first + atomicAdd(ticket, 1u);
       *s_ovf = 0;
-      *s_row = t >= nrows ? -1 : rows[t < nhuge ? t : list_len - 1 - (t - nhuge)];
+      *s_row = t >= t_end ? -1 : rows[t < nhuge ? t : list_len - 1 - (t - nhuge)];
     }
     __syncthreads();
     const int32_t e = *s_row;
@@ -1436,7 +1458,7 @@ __global__ __launch_bounds__(kSpNT, SLG_SP_MINB) void k_walk_sparse(
                         ? buf + (long long)blockIdx.x * buf_stride
                         : nullptr;
     int lgb, lgt;
-    sp_sizes(work, &lgb, &lgt);
+    sp_sizes(work, LGT, &lgb, &lgt);
     const int32_t T = 1 << lgt;
     {
       const long long t1 = clock64();
@@ -1561,7 +1583,7 @@ __global__ __launch_bounds__(kSpNT, SLG_SP_MINB) void k_walk_sparse(
     // 3. candidates with count >= s, in ascending f at tab[at, at + n)
     int32_t at = 0, used = T;
     // (ordering n survivors needs 2 n + 32 slots of the table)
-    const int32_t n = table_collect<kSpNT, kSpSPT, (SLG_SP_RUNS != 0)>(
+    const int32_t n = table_collect<kSpNT, kSPT, (SLG_SP_RUNS != 0)>(
         tab, T, smin, emit, ws, &at, &used, (T - 32) / 2);
     if (n < 0) {  // uniform: hand the row to the giant bin, as for an overflow
       __syncthreads();
@@ -1604,9 +1626,12 @@ using CfgS = CtaCfg<256, 2 * kCtaSMaxWork>;
 using CfgL = CtaCfg<256, 2 * kCtaLMaxWork>;
 #define K_CTA_S k_walk_cta<256, 2 * kCtaSMaxWork, kBinCtaS, 4>
 #define K_CTA_L k_walk_cta<256, 2 * kCtaLMaxWork, kBinCtaL, 3>
+#define K_SP_BIG k_walk_sparse<kSpLgT, SLG_SP_MINB>
+#define K_SP_SMALL k_walk_sparse<kSpSmallLgT, SLG_SP_SMALL_MINB>
 
 struct Occ {
   int sms = 0, warp_blocks = 0, s_blocks = 0, l_blocks = 0, g_blocks = 0, sp_blocks = 0;
+  int sp_small_blocks = 0;
   int dev = -1;
 };
 
@@ -1629,11 +1654,16 @@ Occ &occ_for_device() {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.g_blocks, k_walk_giant, kGiantNT,
                                                   giant_smem());
     if (o.g_blocks < 1) o.g_blocks = 1;
-    cudaFuncSetAttribute(k_walk_sparse, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sparse_smem());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.sp_blocks, k_walk_sparse, kSpNT,
-                                                  sparse_smem());
+    cudaFuncSetAttribute(K_SP_BIG, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sparse_smem(kSpLgT));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.sp_blocks, K_SP_BIG, kSpNT,
+                                                  sparse_smem(kSpLgT));
     if (o.sp_blocks < 1) o.sp_blocks = 1;
+    cudaFuncSetAttribute(K_SP_SMALL, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sparse_smem(kSpSmallLgT));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.sp_small_blocks, K_SP_SMALL, kSpNT,
+                                                  sparse_smem(kSpSmallLgT));
+    if (o.sp_small_blocks < 1) o.sp_small_blocks = 1;
     o.dev = dev;
   }
   return o;
@@ -1650,7 +1680,7 @@ int giant_ctas() { return giant_ctas_for_device(); }
 
 int sparse_ctas() {
   Occ &o = occ_for_device();
-  return o.sms * o.sp_blocks;
+  return o.sms * std::max(o.sp_blocks, SLG_SP_BIG_WORK > 0 ? o.sp_small_blocks : 0);
 }
 
 cudaError_t launch_walk(const WalkLaunch &L, cudaStream_t st, int32_t *launches,
@@ -1676,14 +1706,24 @@ cudaError_t launch_walk(const WalkLaunch &L, cudaStream_t st, int32_t *launches,
   // overflow its table is appended to the giant bin's list
   // the sparse CTAs share the giant bin's scratch out (it holds at least
   // 4 x max(giant, sparse row work) ints per giant CTA)
-  const long long buf_stride =
-      L.giant_scratch ? (L.giant_stride * (long long)(o.sms * o.g_blocks) /
-                         (long long)(o.sms * o.sp_blocks)) & ~31ll
-                      : 0;
-  k_walk_sparse<<<o.sms * o.sp_blocks, kSpNT, sparse_smem(), st>>>(
-      L.w, lists + 4 * stride, L.a, const_cast<int32_t *>(lists) + 3 * stride, (int32_t)stride,
-      L.giant_scratch, buf_stride);
+  auto buf_stride = [&](int ctas) -> long long {
+    return L.giant_scratch
+               ? (L.giant_stride * (long long)(o.sms * o.g_blocks) / (long long)ctas) & ~31ll
+               : 0;
+  };
+  const int sp_big = o.sms * o.sp_blocks;
+  int32_t *giant_list = const_cast<int32_t *>(lists) + 3 * stride;
+  K_SP_BIG<<<sp_big, kSpNT, sparse_smem(kSpLgT), st>>>(
+      L.w, lists + 4 * stride, L.a, giant_list, (int32_t)stride, L.giant_scratch,
+      buf_stride(sp_big), SLG_SP_BIG_WORK > 0 ? 1 : 0);
   ++n;
+  if (SLG_SP_BIG_WORK > 0) {
+    const int sp_small = o.sms * o.sp_small_blocks;
+    K_SP_SMALL<<<sp_small, kSpNT, sparse_smem(kSpSmallLgT), st>>>(
+        L.w, lists + 4 * stride, L.a, giant_list, (int32_t)stride, L.giant_scratch,
+        buf_stride(sp_small), 2);
+    ++n;
+  }
   if (ev) cudaEventRecord(ev[4], st);
   if (L.giant_scratch) {
     k_walk_giant<<<o.sms * o.g_blocks, kGiantNT, giant_smem(), st>>>(
