@@ -1,7 +1,11 @@
-"""The sparse bin (large rows whose far ends are sparse in their id span,
-s >= 2): a seen-bit per id of a window of the span, repeats counted in a
-small shared table, windows redone at half the width when the table would
-overflow.  Every case is compared with the CPU oracle element by element."""
+"""The sparse bin (rows of 1,025 to 16,384 wedges with s >= 2, above the CTA
+bins only when their far ends are sparse in their id span): a first pass
+marks far ends seen twice in a Bloom filter and claims them as candidates
+in a shared table, a second pass counts the candidates' wedges exactly.
+Rows above 8,192 wedges run in the kernel instance with the larger table,
+the others in the one with the smaller table; a row whose candidates or
+survivors do not fit its table is handed to the giant bin.  Every case is
+compared with the CPU oracle element by element."""
 import numpy as np
 import pytest
 
@@ -66,10 +70,9 @@ def test_window_overflow_split(k):
 
 
 def test_rows_across_two_windows():
-    # The dual of a Chung-Lu hypergraph with 1.5M vertices: the rows of the
-    # first ~450K vertices span more than one window of 2^20 ids.  Large
-    # sparse rows at or below 8192 wedges keep their far ends in shared
-    # memory; the larger ones walk again for the second window.
+    # The dual of a Chung-Lu hypergraph with 1.5M vertices: long rows whose
+    # far ends spread over an id span of up to 1.5M (a Bloom filter of at
+    # most 2^17 bits per row), on both sides of the 8,192-wedge split.
     h = hg.chung_lu(200_000, 1_500_000, seed=33, size_cap=10_000)
     dh = slg.to_device(h)
     m, n, off, idx = oracle.side(h, True)
@@ -89,3 +92,49 @@ def test_rows_across_two_windows():
         key = i.long() * m + j.long()
         assert bool(torch.all(key[1:] > key[:-1])) and bool(torch.all(w >= s))
         assert i.shape[0] == slg.count(dh, s, dual=True)
+
+
+def split_rows(m=200_000, n=400_000, seed=8):
+    """Small random hyperedges (1 to 4 of vertices 1000 .. n-1) plus hubs:
+    row 0 holds hubs 0..19, each also in 640 random hyperedges (about
+    12,800 wedges at s = 2, 9,900 at s = 3: the larger-table instance); row
+    1 holds hubs 20..29, each in 500 (about 5,000: the smaller-table
+    instance); row 2 holds hubs 30 and 31, both in the same 3,000 random
+    hyperedges, so that row 2 has 3,000 far ends of two wedges each, more
+    distinct candidates than a 2,048-slot table holds, and every one of
+    those 3,000 rows meets the others in two vertices.  All far ends spread
+    over ids up to m: the rows are sparse in their span."""
+    rng = np.random.default_rng(seed)
+    size = rng.integers(1, 5, m)
+    r = [np.repeat(np.arange(m), size), np.zeros(20, np.int64), np.ones(10, np.int64),
+         np.full(2, 2)]
+    c = [rng.integers(1000, n, int(size.sum())), np.arange(20), np.arange(20, 30),
+         np.array([30, 31])]
+    for hub in range(30):
+        f = rng.choice(np.arange(3, m), 640 if hub < 20 else 500, replace=False)
+        r.append(f)
+        c.append(np.full(f.shape[0], hub))
+    f = rng.choice(np.arange(3, m), 3000, replace=False)
+    r += [f, f]
+    c += [np.full(3000, 30), np.full(3000, 31)]
+    return hg.from_pairs(np.concatenate(r), np.concatenate(c), m, n)
+
+
+@pytest.mark.parametrize("s", [2, 3])
+def test_two_instances_and_hand_off(s):
+    from test_shard_cpu import row_work_by_definition
+    h = split_rows()
+    work = row_work_by_definition(h, s, False)
+    assert work[0] > 8192 and 1024 < work[1] <= 8192 and 1024 < work[2] <= 8192
+    dh = slg.to_device(h)
+    want = oracle.canonical(*oracle.line_graph_of(h, s, threads=8))
+    got = as_np(slg.build(dh, s))
+    st = slg.last_stats()
+    assert st["rows_bin"][4] >= 3, "rows 0, 1 and 2 take the sparse bin"
+    # row 2's 3,000 candidates cannot fit the smaller table: handed over
+    assert st["rows_bin"][3] >= 1, "no sparse row was handed to the giant bin"
+    assert np.array_equal(got, want)
+    i, j, w = slg.build(dh, s, unweighted=True)
+    assert w is None
+    assert np.array_equal(np.stack([i.cpu().numpy(), j.cpu().numpy()], 1), want[:, :2])
+    assert slg.count(dh, s) == want.shape[0]
